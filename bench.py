@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched PBD-R substep on one GB300 (or N, one per rank).
+
+Workload: 4096 independent scenes, each with 1-32 rigid bodies of
+{27, 64, 125, 343} particles (log-uniform body count, uniform sizes), seeded
+random poses and velocities, r = 0.05 m, mu = 0.5, dt = 1/240 s, 10 solver
+iterations: about 5 M particles.  One step = one PBD-R substep of every scene
+(integration, neighbour build, 10 iterations), issued as one batched
+pbdr_step call.  Metric: particle-iterations per second.
+
+Printed (rank 0, one JSON line): the batched throughput (CUDA events on the
+launching stream, inputs resident in HBM and larger than L2), the end-to-end
+throughput through the C ABI with pinned host buffers copied in and out every
+step, the one-scene-per-launch throughput on a sample of the same scenes,
+p50/p99 substep latency, the dominant kernel's roofline fraction, SM clocks
+sampled during the timed region, and the FP64 CPU oracle timed on the host
+cores (cpu_baseline).  ``--impl reference`` times that oracle alone on the
+same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PBD-R particle-iters/s batched vs per-scene launch; p50/p99 step latency"
+UNIT = "particle-iters/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pbdr", choices=["pbdr", "reference"])
+    ap.add_argument("--scenes", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--per-scene-sample", type=int, default=256)
+    ap.add_argument("--per-scene-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-scenes", type=int, default=4096)
+    ap.add_argument("--cpu-substeps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample-scenes", type=int, default=256)
+    ap.add_argument("--settle", type=int, default=240,
+                    help="substeps run before the warm-up so that bodies have landed and touch")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def workload_config(scs, args, extra=None):
+    n = sum(s.num_particles for s in scs)
+    b = sum(s.num_bodies for s in scs)
+    cfg = {
+        "workload": (f"batched: {args.scenes} scenes x 1-32 rigid bodies of {{27,64,125,343}} "
+                     f"particles, seed {args.seed}, r=0.05 m, mu=0.5, dt=1/240 s, 10 iterations"),
+        "scenes": len(scs), "particles": n, "bodies": b, "iterations": 10, "dt": 1.0 / 240.0,
+        "step": "one PBD-R substep of all scenes in one batched pbdr_step",
+        "state": (f"after {args.settle} settling substeps ({args.settle / 240.0:.2f} s simulated) "
+                  "from the seeded start, so bodies rest on the ground and on each other"),
+        "l2": "inputs larger than L2 (state ~%d MB >> 129 MB)" % (n * 80 // (1 << 20)),
+        "parallelism": "scene batch per GPU",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def make_workload(args, seed):
+    from paper_2603_14634_gb300 import scenes
+    return scenes.batched_scenes(args.scenes, seed=seed, workers=min(os.cpu_count() or 1, 32))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_throughput(scs, substeps, threads):
+    """Times the FP64 oracle on the scenes (each advanced `substeps`),
+    spread over `threads` host threads (ctypes releases the GIL).
+    Returns (particle-iters/s, seconds, particle-iters)."""
+    from oracle import oracle as O
+    O.build()
+    objs = [O.OracleScene(s) for s in scs]
+    work = sum(s.num_particles * s.iterations for s in scs) * substeps
+
+    def run(o):
+        o.substep(substeps)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, objs))
+    dt = time.perf_counter() - t0
+    return work / dt, dt, work
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_sha():
+    src = os.path.join(ROOT, "paper_2603_14634_gb300", "csrc", "pbdr_kernels.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic_per_particle_iter():
+    """DRAM bytes per particle-iteration of k_iterate from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    sha = kernel_source_sha()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*k_iterate*.md")):
+        txt = open(path).read()
+        m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+        m_val = re.search(r"dram_bytes_per_particle_iter:\s*([0-9.]+)", txt)
+        if m_sha and m_val and m_sha.group(1) == sha:
+            return float(m_val.group(1))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_pbdr(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2603_14634_gb300.binding import Context
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    scs = make_workload(args, args.seed + rank)     # weak scaling: own batch per rank
+    ctx = Context(local_rank)
+    ids = [ctx.create_scene(s) for s in scs]
+    n_particles = sum(s.num_particles for s in scs)
+    work_per_step = sum(s.num_particles * s.iterations for s in scs)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        if args.settle > 0:
+            ctx.step(ids, args.settle, sh)
+        for _ in range(args.warmup):
+            ctx.step(ids, 1, sh)
+        stream.synchronize()
+        kbar = ctx.neighbor_total(ids, sh) / max(n_particles, 1)
+        launches_per_step = ctx.last_launch_count()
+
+        # ---- timed region: K batched substeps, inputs resident in HBM ----
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        ctx.set_profiling(True)
+        ctx.read_profile()
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            ctx.step(ids, 1, sh)
+            ev[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        prof = ctx.read_profile()
+        ctx.set_profiling(False)
+        ms_total = t_start.elapsed_time(t_end)
+        lat = sorted(a.elapsed_time(b) for a, b in ev)
+
+    ms_max = ms_total
+    total_work = work_per_step * args.steps
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        w = torch.tensor([float(total_work)], device="cuda")
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        total_work = float(w.item())
+    value = total_work / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    pos_h = torch.empty((n_particles, 3), dtype=torch.float32, pin_memory=True).numpy()
+    vel_h = torch.empty((n_particles, 3), dtype=torch.float32, pin_memory=True).numpy()
+    with torch.cuda.stream(stream):
+        ctx.read_states(ids, pos_h, vel_h, sh)
+        e2e_steps = max(1, min(args.e2e_steps, args.steps))
+        for k in range(2):   # warm the staging buffers
+            ctx.write_states(ids, pos_h, vel_h, sh)
+            ctx.step(ids, 1, sh)
+            ctx.read_states(ids, pos_h, vel_h, sh)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            ctx.write_states(ids, pos_h, vel_h, sh)
+            ctx.step(ids, 1, sh)
+            ctx.read_states(ids, pos_h, vel_h, sh)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = work_per_step * world * e2e_steps / e2e_s
+
+    # ---- one scene per launch on a sample of the same scenes ----
+    sample = ids[:: max(1, len(ids) // max(1, args.per_scene_sample))][: args.per_scene_sample]
+    s_work = sum(scs[i].num_particles * scs[i].iterations for i in sample)
+    with torch.cuda.stream(stream):
+        for sid in sample:
+            ctx.step([sid], 1, sh)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.per_scene_steps):
+            for sid in sample:
+                ctx.step([sid], 1, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ps_ms = a.elapsed_time(b)
+    per_scene_value = s_work * args.per_scene_steps / (ps_ms * 1e-3)
+    # the batched path on the same sample, for a like-for-like ratio
+    with torch.cuda.stream(stream):
+        ctx.step(sample, 1, sh)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.per_scene_steps):
+            ctx.step(sample, 1, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        bs_ms = a.elapsed_time(b)
+    batched_sample_value = s_work * args.per_scene_steps / (bs_ms * 1e-3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    # ---- roofline of the dominant kernel (k_iterate, one launch per iteration) ----
+    it_ms, it_launches = prof["iterate"]
+    avg_launch_s = it_ms * 1e-3 / max(it_launches, 1)
+    bytes_per_pi = 84.0 + 4.0 * kbar
+    bytes_per_launch = bytes_per_pi * n_particles
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_src = hbm_peak()
+    tr = ncu_traffic_per_particle_iter()
+    roofline = {
+        "bound": "hbm", "kernel": "k_iterate", "achieved": round(achieved, 1), "peak": peak,
+        "unit": "GB/s", "frac": round(achieved / peak, 4),
+        "traffic": None if tr is None else round(tr * n_particles),
+        "algorithmic_bytes_per_particle_iter": round(bytes_per_pi, 2), "kbar": round(kbar, 3),
+        "avg_launch_us": round(avg_launch_s * 1e6, 2), "peak_source": peak_src,
+        "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+    }
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(scs, args),
+        "p50_step_ms": round(lat[len(lat) // 2], 4),
+        "p99_step_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
+        "per_scene_launch": {
+            "value": round(per_scene_value, 1), "unit": UNIT, "sample_scenes": len(sample),
+            "batched_same_sample": round(batched_sample_value, 1),
+            "batched_over_per_scene": round(batched_sample_value / per_scene_value, 2)},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(n_particles * 24),
+                "d2h_bytes_per_step": int(n_particles * 24 + 4 * len(ids)), "steps": e2e_steps,
+                "path": "pbdr_write_states + pbdr_step + pbdr_read_states, pinned host buffers"},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_scs = scs[: args.cpu_scenes]
+        thr = host_cores()
+        v, secs, work = oracle_throughput(cpu_scs, args.cpu_substeps, thr)
+        line["cpu_baseline"] = {
+            "value": round(v, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": (f"first {len(cpu_scs)} scenes of the workload x {args.cpu_substeps} "
+                       f"substeps from the seeded start, FP64 C oracle, one scene per host thread "
+                       f"({work} particle-iters in {secs:.1f} s)")}
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def run_reference(args, rank):
+    """The reference arm: the FP64 oracle as it stands on the host cores;
+    each step advances a bounded sample of the workload by one substep."""
+    if rank != 0:
+        return None
+    scs = make_workload(args, args.seed)
+    sample = scs[: args.ref_sample_scenes]
+    thr = host_cores()
+    for _ in range(args.warmup):
+        oracle_throughput(sample, 1, thr)
+    times = []
+    work = 0
+    for _ in range(args.steps):
+        v, secs, w = oracle_throughput(sample, 1, thr)
+        times.append(secs)
+        work += w
+    total = sum(times)
+    value = work / total
+    cpu = {"value": round(value, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
+           "sample": f"first {len(sample)} scenes of the workload, one substep per step, FP64 C oracle"}
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(scs, args, {"reference_sample_scenes": len(sample)}),
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        from paper_2603_14634_gb300 import build as B
+        if rank == 0 or world == 1:
+            B.build()
+        line = run_pbdr(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

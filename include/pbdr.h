@@ -1,0 +1,196 @@
+/*
+ * pbdr.h - C ABI of the GB300 (sm_103a) PBD-R solver.
+ *
+ * PBD-R ("Physically Accurate Rigid-Body Dynamics in Particle-Based
+ * Simulation", arXiv 2603.14634) steps rigid bodies made of equal spheres
+ * ("particles") with position-based dynamics.  One substep is Algorithm 1:
+ *   - integration:  v~ = v + dt w f_ext(x),  x~ = x + dt v~       (Alg. 1, l.1-4)
+ *   - K solver iterations, each:                                    (Alg. 1, l.5-11)
+ *       ground contact dX_PG and particle-particle contact dX_PP between
+ *       particles of different bodies, with Coulomb friction (Sec. III-A),
+ *       shape matching dX_SM toward the best rigid fit of the rest shape
+ *       (Sec. III-A (3), Sec. III-C),
+ *       incremental velocity update V_{i+1} = V_i + dX/dt (Sec. III-B, Eqs. 1-2),
+ *       momentum enforcement: uniform dv and rigid w corrections restoring the
+ *       linear and angular momentum of the body before shape matching
+ *       (Sec. III-C, Eqs. lin_momentum and ang_momentum).
+ * Contact candidates are found once per substep on x~ with a hashed uniform
+ * grid (pairs closer than Rn = 2.2 r, FP32 predicate; the paper does not
+ * specify the search).
+ *
+ * Conventions
+ *   - All functions return PBDR_OK (0) or a negative PBDR_ERR_* code; no C++
+ *     exception crosses the ABI.  pbdr_last_error() gives a message for the
+ *     calling thread's last failure.
+ *   - Host arrays are owned by the caller and copied; the library owns every
+ *     device allocation (state, neighbour lists, sort buffers, graphs).
+ *   - Particle order on input and output is the caller's order.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that return device results to host buffers synchronise that stream;
+ *     pbdr_step is asynchronous.
+ *   - A context is bound to one device and is not thread-safe: one thread
+ *     drives a context at a time.
+ *   - Units are SI; state is FP32.
+ */
+#ifndef PBDR_H
+#define PBDR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define PBDR_OK 0
+#define PBDR_ERR_INVALID (-1)      /* bad argument or descriptor */
+#define PBDR_ERR_OOM (-2)          /* device allocation failed */
+#define PBDR_ERR_BUDGET (-3)       /* request exceeds the context's HBM budget */
+#define PBDR_ERR_NBR_OVERFLOW (-4) /* a neighbour list exceeded its capacity */
+#define PBDR_ERR_NONFINITE (-5)    /* a non-finite position was produced */
+#define PBDR_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
+#define PBDR_ERR_CUDA (-7)         /* a CUDA runtime call failed */
+#define PBDR_ERR_UNSUPPORTED (-8)  /* a flag combination this build does not run */
+
+/* per-scene error bits reported by pbdr_read_state / pbdr_read_states */
+#define PBDR_EBIT_NBR_OVERFLOW (1u << 0) /* a neighbour list was truncated */
+#define PBDR_EBIT_NONFINITE (1u << 1)    /* a position became NaN or Inf */
+
+/* scene flags (ablations of Sec. V-C and readings of the paper) */
+#define PBDR_STD_VELOCITY (1u << 0) /* V = (X - X_init)/dt (standard PBD, Sec. III-A) */
+#define PBDR_NO_LINMOM (1u << 1)    /* drop Eq. lin_momentum */
+#define PBDR_NO_ANGMOM (1u << 2)    /* drop Eq. ang_momentum */
+#define PBDR_CONTACT_AVG (1u << 3)  /* average particle-particle corrections per particle */
+#define PBDR_SM_FROM_XI (1u << 4)   /* shape matching on X_i instead of X_i + contacts */
+
+typedef struct pbdr_ctx pbdr_ctx; /* opaque: device state, scene table, plans, graphs */
+typedef int32_t pbdr_scene;       /* scene handle, >= 0 */
+
+/* One independent scene (Sec. III notation).  Particles of body b are
+ * [body_off[b], body_off[b+1]).  The rest shape of each body is its
+ * configuration at creation: q_p = x_p - c_b (Mueller et al. 2005). */
+typedef struct {
+  int32_t num_particles;   /* N >= 0 */
+  int32_t num_bodies;      /* B >= 1 when N > 0 */
+  const float *pos;        /* [N*3] host, xyz per particle */
+  const float *vel;        /* [N*3] host */
+  const float *inv_mass;   /* [N] host, w_p > 0 and finite */
+  const int32_t *body_off; /* [B+1] host, body_off[0] = 0, strictly increasing, body_off[B] = N */
+  float radius;            /* r > 0, equal for every particle of the scene */
+  float friction;          /* mu >= 0 (kinetic coefficient, Table I; static = kinetic) */
+  float gravity[3];        /* m/s^2 */
+  float plane[4];          /* ground n.x = d: n (unit) = plane[0..2], d = plane[3];
+                              particles are kept on the side n.x >= d + r */
+  float dt;                /* substep length > 0 */
+  int32_t iterations;      /* solver iterations K, 1..1024 */
+  uint32_t flags;          /* PBDR_* scene flags */
+} pbdr_scene_desc;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context may hold (0 = no cap).  *out receives the handle.
+ * Errors: PBDR_ERR_INVALID (bad device or NULL out), PBDR_ERR_CUDA. */
+int pbdr_ctx_create(int device, size_t hbm_budget_bytes, pbdr_ctx **out);
+
+/* Frees every device resource of the context.  NULL is accepted. */
+int pbdr_ctx_destroy(pbdr_ctx *ctx);
+
+/* Copies a scene into device memory (synchronous) and returns its handle.
+ * Computes M_b, c_b and the rest offsets in FP64 on the host.
+ * Errors: PBDR_ERR_INVALID (descriptor check failed: sizes, offsets, masses,
+ * radius, dt, iterations, plane normal), PBDR_ERR_BUDGET, PBDR_ERR_OOM,
+ * PBDR_ERR_UNSUPPORTED (flags). */
+int pbdr_create_scene(pbdr_ctx *ctx, const pbdr_scene_desc *desc, pbdr_scene *out);
+
+/* Removes a scene from the context; its handle becomes invalid. */
+int pbdr_destroy_scene(pbdr_ctx *ctx, pbdr_scene scene);
+
+/* Sets a constant external force F (N) at the centre of mass and a constant
+ * torque tau (N m) about it on one body (the f_ext of Alg. 1 line 2 for the
+ * pushed-box and box-with-torque tests of Table I).  Each particle receives
+ * F/M + alpha x (x - c) with alpha = I^-1 tau, c and I taken at the start of
+ * the substep.  Zero F and tau remove the wrench.  Synchronous. */
+int pbdr_set_body_wrench(pbdr_ctx *ctx, pbdr_scene scene, int32_t body,
+                         const float F[3], const float tau[3]);
+
+/* Advances the n scenes ids[0..n) by `substeps` PBD-R substeps (Algorithm 1)
+ * on `stream`, asynchronously.  All scenes of one call are stepped together
+ * in the same kernels (batched); scenes are independent.  Results are
+ * bit-identical whatever other scenes share the call.
+ * Errors: PBDR_ERR_INVALID (bad handle, duplicate id, n < 1, substeps < 0),
+ * PBDR_ERR_OOM, PBDR_ERR_CUDA.  Device-side problems (neighbour overflow,
+ * non-finite positions) are reported per scene by pbdr_read_state. */
+int pbdr_step(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int32_t substeps,
+              void *stream);
+
+/* Copies one scene's state to host buffers pos, vel ([N*3] each, may be
+ * NULL) and its error bits to *err_bits (may be NULL; bits are cleared by
+ * the read), then synchronises `stream`. */
+int pbdr_read_state(pbdr_ctx *ctx, pbdr_scene scene, float *pos, float *vel,
+                    uint32_t *err_bits, void *stream);
+
+/* Overwrites one scene's state from host buffers pos, vel ([N*3] each; NULL
+ * leaves that part unchanged) on `stream`; the host buffers must stay valid
+ * until the stream reaches this point (pbdr_read_state or a stream sync).
+ * The rest shape is not changed. */
+int pbdr_write_state(pbdr_ctx *ctx, pbdr_scene scene, const float *pos,
+                     const float *vel, void *stream);
+
+/* Batched forms: the scenes' particles are concatenated in the order of ids
+ * (host buffers [sum N_s * 3]); err_bits is [n] (may be NULL).  One device
+ * gather/scatter plus one copy each way.  read synchronises `stream`. */
+int pbdr_read_states(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, float *pos,
+                     float *vel, uint32_t *err_bits, void *stream);
+int pbdr_write_states(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n,
+                      const float *pos, const float *vel, void *stream);
+
+/* Number of particles and bodies of a scene (either pointer may be NULL). */
+int pbdr_scene_info(pbdr_ctx *ctx, pbdr_scene scene, int32_t *num_particles,
+                    int32_t *num_bodies);
+
+/* Message of the calling thread's last error ("" if none).  The pointer stays
+ * valid until the thread's next pbdr_* call. */
+const char *pbdr_last_error(void);
+
+/* ---- inspection (tests and profiling) ---------------------------------- */
+
+/* Runs only the neighbour stage (cell keys, radix sort, cell ranges,
+ * neighbour lists) of the scenes ids[0..n) on their CURRENT positions, taken
+ * as the predicted positions x~; the state is not modified. */
+int pbdr_build_neighbors(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, void *stream);
+
+/* Reads one scene's result of the last neighbour stage, in scene-local
+ * numbering: sorted_key[N] (bucket in [0, T_s), T_s = smallest power of two
+ * >= 2N) and sorted_id[N] (particle index), sorted by key and by id within a
+ * key; off[N+1] and idx (ascending neighbour indices of each particle, CSR).
+ * idx_cap bounds idx; *idx_count receives the total.  Any pointer except
+ * idx_count may be NULL.  Synchronises `stream`. */
+int pbdr_read_neighbors(pbdr_ctx *ctx, pbdr_scene scene, uint32_t *sorted_key,
+                        uint32_t *sorted_id, int32_t *off, int32_t *idx,
+                        int64_t idx_cap, int64_t *idx_count, void *stream);
+
+/* Launch statistics of the last pbdr_step call: the number of kernel
+ * launches it issued (graph nodes counted individually). */
+int pbdr_last_launch_count(pbdr_ctx *ctx, int64_t *launches);
+
+/* Sum of the neighbour-list lengths of the scenes ids[0..n) from the last
+ * neighbour stage (the mean list length kbar = total / particles).
+ * Synchronises `stream`. */
+int pbdr_neighbor_total(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int64_t *total,
+                        void *stream);
+
+/* Stage timing.  While enabled, pbdr_step records CUDA events on its stream
+ * around each stage of every substep (no CUDA graph is used).  Stages:
+ * 0 wrench, 1 integration + cell keys, 2 radix sort, 3 cell ranges +
+ * neighbour lists, 4 solver iterations (all K launches).  pbdr_read_profile
+ * synchronises, returns the summed milliseconds and launch counts per stage
+ * (arrays of `nstages` <= 5 entries) and resets the accumulators. */
+#define PBDR_NUM_STAGES 5
+int pbdr_set_profiling(pbdr_ctx *ctx, int enable);
+int pbdr_read_profile(pbdr_ctx *ctx, double *stage_ms, int64_t *stage_launches, int32_t nstages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBDR_H */

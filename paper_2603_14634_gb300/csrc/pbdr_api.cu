@@ -1,0 +1,915 @@
+// C ABI of the PBD-R library: context, packed scene table, step plans and the
+// host side of one substep.  See include/pbdr.h for the contract of every
+// entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pbdr_internal.cuh"
+
+using namespace pbdr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? PBDR_ERR_OOM : PBDR_ERR_CUDA,   \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+// owned device allocation
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+uint32_t table_size(int32_t n) {
+  uint32_t want = (uint32_t)std::max(n, 1) * 2u;
+  uint32_t t = 1;
+  while (t < want) t <<= 1;
+  return t;
+}
+
+struct SceneHost {
+  bool alive = false;
+  int32_t p0 = 0, np = 0, b0 = 0, nb = 0;
+  ScenePar par{};
+  int wrench_bodies = 0;
+};
+
+struct Plan {
+  std::vector<int32_t> ids;
+  int32_t np = 0, nb = 0;
+  int32_t pbase = 0, bbase = 0;
+  bool pcontig = true, bcontig = true;
+  DevBuf pmap, bmap, hbase;
+  uint32_t T_total = 0;
+  int key_bits = 0;
+  DevBuf keys_a, keys_b, vals_a, vals_b, hist, cstart, cend, spos;
+  std::vector<int32_t> wrench_list;
+  DevBuf wlist;
+  int kmax = 0;
+  bool std_any = false;
+  std::vector<int64_t> seg_off;    // per plan scene: first plan particle (n+1)
+  std::vector<uint32_t> hbase_host;
+  int sorted_in_b = 0;             // where the last sort left its result
+};
+
+}  // namespace
+
+struct pbdr_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  int32_t pcap = 0, bcap = 0, scap = 0;
+  int32_t np_used = 0, nb_used = 0;
+  int nbr_cap = 32;
+  DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
+  DevBuf bodies, wrench, quat, bcom;
+  DevBuf scenes, scene_err;
+  std::vector<SceneHost> sh;
+  std::vector<BodyRec> bh;
+  std::vector<BodyWrench> wh;
+  std::map<std::vector<int32_t>, std::unique_ptr<Plan>> plans;
+  Plan *last_nbr_plan = nullptr;
+  int64_t last_launches = 0;
+  DevBuf stage_pos, stage_vel, seg_p0, seg_off, err_ids, err_out;
+  // stage profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Mark { int stage; size_t e0, e1; int64_t launches; };
+  std::vector<Mark> marks;
+  double stage_ms[PBDR_NUM_STAGES] = {0};
+  int64_t stage_launches[PBDR_NUM_STAGES] = {0};
+};
+
+namespace {
+
+int dev_alloc(pbdr_ctx *c, DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return PBDR_OK;
+  size_t freed = b.bytes;
+  if (c->budget && c->used - freed + bytes > c->budget)
+    return fail(PBDR_ERR_BUDGET, "device memory budget exceeded (" + std::to_string(c->used - freed + bytes) +
+                                     " > " + std::to_string(c->budget) + " bytes)");
+  b.release();
+  c->used -= freed;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return fail(PBDR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  c->used += bytes;
+  return PBDR_OK;
+}
+
+void dev_free(pbdr_ctx *c, DevBuf &b) {
+  c->used -= b.bytes;
+  b.release();
+}
+
+// grow `b` to `bytes`, keeping the first `keep` bytes
+int dev_grow(pbdr_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
+  if (b.bytes >= bytes) return PBDR_OK;
+  if (c->budget && c->used + bytes > c->budget)
+    return fail(PBDR_ERR_BUDGET, "device memory budget exceeded");
+  void *np = nullptr;
+  cudaError_t e = cudaMalloc(&np, bytes);
+  if (e != cudaSuccess) return fail(PBDR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (b.p && keep) {
+    e = cudaMemcpy(np, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(np);
+      return fail(PBDR_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+  }
+  c->used += bytes;
+  dev_free(c, b);
+  b.p = np;
+  b.bytes = bytes;
+  return PBDR_OK;
+}
+
+int ensure_capacity(pbdr_ctx *c, int32_t np_need, int32_t nb_need, int32_t ns_need) {
+  int rc;
+  if (np_need > c->pcap) {
+    int32_t cap = std::max(np_need, std::max(1024, c->pcap * 2));
+    size_t keep4 = (size_t)c->np_used * sizeof(float4);
+    for (int k = 0; k < 2; ++k) {
+      if ((rc = dev_grow(c, c->X[k], (size_t)cap * sizeof(float4), keep4))) return rc;
+      if ((rc = dev_grow(c, c->V[k], (size_t)cap * sizeof(float4), keep4))) return rc;
+    }
+    if ((rc = dev_grow(c, c->Q, (size_t)cap * sizeof(float4), keep4))) return rc;
+    if ((rc = dev_grow(c, c->pbody, (size_t)cap * sizeof(int32_t), (size_t)c->np_used * 4))) return rc;
+    if ((rc = dev_grow(c, c->nbr_cnt, (size_t)cap * sizeof(int32_t), 0))) return rc;
+    // neighbour slots are rebuilt every substep: no copy
+    dev_free(c, c->nbr);
+    if ((rc = dev_alloc(c, c->nbr, (size_t)cap * c->nbr_cap * sizeof(int32_t)))) return rc;
+    if (c->Xinit.p) {
+      dev_free(c, c->Xinit);
+      if ((rc = dev_alloc(c, c->Xinit, (size_t)cap * sizeof(float4)))) return rc;
+    }
+    c->pcap = cap;
+  }
+  if (nb_need > c->bcap) {
+    int32_t cap = std::max(nb_need, std::max(256, c->bcap * 2));
+    if ((rc = dev_grow(c, c->bodies, (size_t)cap * sizeof(BodyRec), (size_t)c->nb_used * sizeof(BodyRec)))) return rc;
+    if ((rc = dev_grow(c, c->wrench, (size_t)cap * sizeof(BodyWrench), (size_t)c->nb_used * sizeof(BodyWrench)))) return rc;
+    if ((rc = dev_grow(c, c->quat, (size_t)cap * sizeof(float4), (size_t)c->nb_used * sizeof(float4)))) return rc;
+    if ((rc = dev_grow(c, c->bcom, (size_t)cap * sizeof(float4), (size_t)c->nb_used * sizeof(float4)))) return rc;
+    c->bcap = cap;
+  }
+  if (ns_need > c->scap) {
+    int32_t cap = std::max(ns_need, std::max(64, c->scap * 2));
+    size_t ns = c->sh.size();
+    if ((rc = dev_grow(c, c->scenes, (size_t)cap * sizeof(ScenePar), ns * sizeof(ScenePar)))) return rc;
+    if ((rc = dev_grow(c, c->scene_err, (size_t)cap * sizeof(uint32_t), ns * sizeof(uint32_t)))) return rc;
+    c->scap = cap;
+  }
+  return PBDR_OK;
+}
+
+bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int check_scene(pbdr_ctx *c, pbdr_scene s) {
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  if (s < 0 || s >= (int32_t)c->sh.size() || !c->sh[s].alive)
+    return fail(PBDR_ERR_INVALID, "invalid scene handle " + std::to_string(s));
+  return PBDR_OK;
+}
+
+int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) {
+  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
+  std::vector<int32_t> key(ids, ids + n);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    *out = it->second.get();
+    return PBDR_OK;
+  }
+  std::vector<char> seen(c->sh.size(), 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = check_scene(c, ids[i]);
+    if (rc) return rc;
+    if (seen[ids[i]]) return fail(PBDR_ERR_INVALID, "duplicate scene id " + std::to_string(ids[i]));
+    seen[ids[i]] = 1;
+  }
+  auto P = std::make_unique<Plan>();
+  P->ids = key;
+  std::vector<int32_t> pmap, bmap;
+  P->hbase_host.assign(std::max<size_t>(c->sh.size(), 1), 0u);
+  P->seg_off.push_back(0);
+  uint64_t tsum = 0;
+  int32_t next_p = -1, next_b = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    const SceneHost &S = c->sh[ids[i]];
+    if (i == 0) {
+      P->pbase = S.p0;
+      P->bbase = S.b0;
+    } else {
+      if (S.p0 != next_p) P->pcontig = false;
+      if (S.b0 != next_b) P->bcontig = false;
+    }
+    next_p = S.p0 + S.np;
+    next_b = S.b0 + S.nb;
+    for (int32_t k = 0; k < S.np; ++k) pmap.push_back(S.p0 + k);
+    for (int32_t k = 0; k < S.nb; ++k) bmap.push_back(S.b0 + k);
+    P->hbase_host[ids[i]] = (uint32_t)tsum;
+    tsum += S.par.T;
+    if (tsum > 0xF0000000ull) return fail(PBDR_ERR_INVALID, "hash tables of one step exceed 2^32 buckets");
+    P->np += S.np;
+    P->nb += S.nb;
+    P->seg_off.push_back(P->np);
+    P->kmax = std::max(P->kmax, S.par.iterations);
+    P->std_any |= (S.par.flags & kStdVelocity) != 0;
+    if (S.wrench_bodies)
+      for (int32_t b = S.b0; b < S.b0 + S.nb; ++b)
+        if (c->bh[b].has_wrench) P->wrench_list.push_back(b);
+  }
+  P->T_total = (uint32_t)tsum;
+  int bits = 1;
+  while (bits < 32 && (1ull << bits) < tsum) ++bits;
+  P->key_bits = bits;
+  int rc;
+  if (!P->pcontig) {
+    if ((rc = dev_alloc(c, P->pmap, pmap.size() * 4))) return rc;
+    CUDA_TRY(cudaMemcpy(P->pmap.p, pmap.data(), pmap.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (!P->bcontig) {
+    if ((rc = dev_alloc(c, P->bmap, bmap.size() * 4))) return rc;
+    CUDA_TRY(cudaMemcpy(P->bmap.p, bmap.data(), bmap.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if ((rc = dev_alloc(c, P->hbase, P->hbase_host.size() * 4))) return rc;
+  CUDA_TRY(cudaMemcpy(P->hbase.p, P->hbase_host.data(), P->hbase_host.size() * 4, cudaMemcpyHostToDevice));
+  const size_t npb = (size_t)std::max(P->np, 1);
+  if ((rc = dev_alloc(c, P->keys_a, npb * 4))) return rc;
+  if ((rc = dev_alloc(c, P->keys_b, npb * 4))) return rc;
+  if ((rc = dev_alloc(c, P->vals_a, npb * 4))) return rc;
+  if ((rc = dev_alloc(c, P->vals_b, npb * 4))) return rc;
+  if ((rc = dev_alloc(c, P->spos, npb * sizeof(float4)))) return rc;
+  if ((rc = dev_alloc(c, P->hist, radix_hist_words(P->np) * 4))) return rc;
+  if ((rc = dev_alloc(c, P->cstart, (size_t)std::max<uint32_t>(P->T_total, 1) * 4))) return rc;
+  if ((rc = dev_alloc(c, P->cend, (size_t)std::max<uint32_t>(P->T_total, 1) * 4))) return rc;
+  if (!P->wrench_list.empty()) {
+    if ((rc = dev_alloc(c, P->wlist, P->wrench_list.size() * 4))) return rc;
+    CUDA_TRY(cudaMemcpy(P->wlist.p, P->wrench_list.data(), P->wrench_list.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (P->std_any && !c->Xinit.p) {
+    if ((rc = dev_alloc(c, c->Xinit, (size_t)c->pcap * sizeof(float4)))) return rc;
+  }
+  *out = P.get();
+  c->plans[key] = std::move(P);
+  return PBDR_OK;
+}
+
+void invalidate_plans(pbdr_ctx *c) {
+  for (auto &kv : c->plans) {
+    Plan &P = *kv.second;
+    for (DevBuf *b : {&P.pmap, &P.bmap, &P.hbase, &P.keys_a, &P.keys_b, &P.vals_a, &P.vals_b,
+                      &P.hist, &P.cstart, &P.cend, &P.spos, &P.wlist})
+      dev_free(c, *b);
+  }
+  c->plans.clear();
+  c->last_nbr_plan = nullptr;
+}
+
+// event of the profiling pool, recorded on s (returns its pool index)
+size_t prof_event(pbdr_ctx *c, cudaStream_t s) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used], s);
+  return c->ev_used++;
+}
+
+struct StageTimer {
+  pbdr_ctx *c;
+  cudaStream_t s;
+  int stage;
+  size_t e0 = 0;
+  int64_t l0 = 0;
+  int64_t &launches;
+  StageTimer(pbdr_ctx *c_, cudaStream_t s_, int st, int64_t &l) : c(c_), s(s_), stage(st), launches(l) {
+    if (c->profiling) {
+      e0 = prof_event(c, s);
+      l0 = launches;
+    }
+  }
+  ~StageTimer() {
+    if (c->profiling) c->marks.push_back({stage, e0, prof_event(c, s), launches - l0});
+  }
+};
+
+// neighbour stage on the positions Xp (keys already written by k_predict)
+int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64_t &launches) {
+  int in_b = 0;
+  {
+  StageTimer tm(c, s, 2, launches);
+  launches += radix_sort_pairs(P.keys_a.as<uint32_t>(), P.vals_a.as<uint32_t>(), P.keys_b.as<uint32_t>(),
+                               P.vals_b.as<uint32_t>(), P.hist.as<uint32_t>(), P.np, P.key_bits, &in_b, s);
+  }
+  P.sorted_in_b = in_b;
+  StageTimer tm(c, s, 3, launches);
+  CUDA_TRY(cudaMemsetAsync(P.cstart.p, 0xFF, (size_t)std::max<uint32_t>(P.T_total, 1) * 4, s));
+  const uint32_t *sk = in_b ? P.keys_b.as<uint32_t>() : P.keys_a.as<uint32_t>();
+  const uint32_t *sv = in_b ? P.vals_b.as<uint32_t>() : P.vals_a.as<uint32_t>();
+  CellArgs ca{};
+  ca.skeys = sk;
+  ca.svals = sv;
+  ca.Xp = Xp;
+  ca.pbody = c->pbody.as<int32_t>();
+  ca.cstart = P.cstart.as<uint32_t>();
+  ca.cend = P.cend.as<uint32_t>();
+  ca.spos = P.spos.as<float4>();
+  ca.np = P.np;
+  launches += launch_cells(ca, s);
+  NbrArgs na{};
+  na.skeys = sk;
+  na.svals = sv;
+  na.Xp = Xp;
+  na.pbody = c->pbody.as<int32_t>();
+  na.pmap = P.pcontig ? nullptr : P.pmap.as<int32_t>();
+  na.pbase = P.pbase;
+  na.spos = P.spos.as<float4>();
+  na.cstart = P.cstart.as<uint32_t>();
+  na.cend = P.cend.as<uint32_t>();
+  na.bodies = c->bodies.as<BodyRec>();
+  na.scenes = c->scenes.as<ScenePar>();
+  na.hbase = P.hbase.as<uint32_t>();
+  na.nbr_cnt = c->nbr_cnt.as<int32_t>();
+  na.nbr = c->nbr.as<int32_t>();
+  na.nbr_stride = c->pcap;
+  na.cap = c->nbr_cap;
+  na.scene_err = c->scene_err.as<uint32_t>();
+  na.np = P.np;
+  launches += launch_neighbors(na, s);
+  c->last_nbr_plan = &P;
+  return PBDR_OK;
+}
+
+PredictArgs predict_args(pbdr_ctx *c, Plan &P, const float4 *X0, const float4 *V0, float4 *Xp,
+                         float4 *Vp, int predict) {
+  PredictArgs a{};
+  a.X0 = X0;
+  a.V0 = V0;
+  a.Xp = Xp;
+  a.Vp = Vp;
+  a.Xinit = (predict && P.std_any) ? c->Xinit.as<float4>() : nullptr;
+  a.pbody = c->pbody.as<int32_t>();
+  a.bodies = c->bodies.as<BodyRec>();
+  a.scenes = c->scenes.as<ScenePar>();
+  a.wrench = c->wrench.as<BodyWrench>();
+  a.pmap = P.pcontig ? nullptr : P.pmap.as<int32_t>();
+  a.pbase = P.pbase;
+  a.np = P.np;
+  a.hbase = P.hbase.as<uint32_t>();
+  a.keys = P.keys_a.as<uint32_t>();
+  a.vals = P.vals_a.as<uint32_t>();
+  a.predict = predict;
+  return a;
+}
+
+int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
+  if (P.np == 0) return PBDR_OK;
+  const int K = P.kmax;
+  float4 *X0 = c->X[0].as<float4>(), *V0 = c->V[0].as<float4>();
+  float4 *X1 = c->X[1].as<float4>(), *V1 = c->V[1].as<float4>();
+  if (!P.wrench_list.empty()) {
+    StageTimer tm(c, s, 0, launches);
+    WrenchArgs wa{};
+    wa.X = X0;
+    wa.Q = c->Q.as<float4>();
+    wa.bodies = c->bodies.as<BodyRec>();
+    wa.wrench = c->wrench.as<BodyWrench>();
+    wa.blist = P.wlist.as<int32_t>();
+    wa.nb = (int32_t)P.wrench_list.size();
+    launches += launch_wrench(wa, s);
+  }
+  // iteration k writes buffer (K-1-k) % 2, so the last one lands in buffer 0;
+  // the prediction writes the buffer iteration 0 reads
+  float4 *Xp = (K % 2 == 1) ? X1 : X0;
+  float4 *Vp = (K % 2 == 1) ? V1 : V0;
+  {
+    StageTimer tm(c, s, 1, launches);
+    launches += launch_predict(predict_args(c, P, X0, V0, Xp, Vp, 1), s);
+  }
+  int rc = neighbor_stage(c, P, Xp, s, launches);
+  if (rc) return rc;
+  StageTimer tm(c, s, 4, launches);
+  IterArgs ia{};
+  ia.Q = c->Q.as<float4>();
+  ia.Xinit = P.std_any ? c->Xinit.as<float4>() : nullptr;
+  ia.nbr_cnt = c->nbr_cnt.as<int32_t>();
+  ia.nbr = c->nbr.as<int32_t>();
+  ia.nbr_stride = c->pcap;
+  ia.bodies = c->bodies.as<BodyRec>();
+  ia.scenes = c->scenes.as<ScenePar>();
+  ia.quat = c->quat.as<float4>();
+  ia.bcom = c->bcom.as<float4>();
+  ia.bmap = P.bcontig ? nullptr : P.bmap.as<int32_t>();
+  ia.bbase = P.bbase;
+  ia.nbodies = P.nb;
+  ia.scene_err = c->scene_err.as<uint32_t>();
+  for (int k = 0; k < K; ++k) {
+    const int out = (K - 1 - k) % 2;
+    ia.Xin = out ? X0 : X1;
+    ia.Vin = out ? V0 : V1;
+    ia.Xout = out ? X1 : X0;
+    ia.Vout = out ? V1 : V0;
+    ia.k = k;
+    launches += launch_iterate(ia, 4, s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return PBDR_OK;
+}
+
+__global__ void k_errs(uint32_t *scene_err, const int32_t *ids, int32_t n, uint32_t *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = scene_err[ids[i]];
+  scene_err[ids[i]] = 0u;
+}
+
+// gather / scatter of xyz state for scenes ids[0..n) through device staging
+int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, float *hvel,
+                    const float *cpos, const float *cvel, uint32_t *err_bits, int unpack,
+                    cudaStream_t s) {
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
+  std::vector<int32_t> p0(n);
+  std::vector<int64_t> off(n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = check_scene(c, ids[i]);
+    if (rc) return rc;
+    p0[i] = c->sh[ids[i]].p0;
+    off[i + 1] = off[i] + c->sh[ids[i]].np;
+  }
+  const int64_t total = off[n];
+  int rc;
+  const bool want_pos = unpack ? cpos != nullptr : hpos != nullptr;
+  const bool want_vel = unpack ? cvel != nullptr : hvel != nullptr;
+  if ((rc = dev_alloc(c, c->seg_p0, (size_t)n * 4))) return rc;
+  if ((rc = dev_alloc(c, c->seg_off, (size_t)(n + 1) * 8))) return rc;
+  if (want_pos && (rc = dev_alloc(c, c->stage_pos, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
+  if (want_vel && (rc = dev_alloc(c, c->stage_vel, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
+  CUDA_TRY(cudaMemcpyAsync(c->seg_p0.p, p0.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->seg_off.p, off.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
+  PackArgs pa{};
+  pa.X = c->X[0].as<float4>();
+  pa.V = c->V[0].as<float4>();
+  pa.hpos = want_pos ? c->stage_pos.as<float>() : nullptr;
+  pa.hvel = want_vel ? c->stage_vel.as<float>() : nullptr;
+  pa.seg_p0 = c->seg_p0.as<int32_t>();
+  pa.seg_off = c->seg_off.as<int64_t>();
+  pa.nseg = n;
+  pa.total = total;
+  if (unpack) {
+    if (want_pos) CUDA_TRY(cudaMemcpyAsync(pa.hpos, cpos, (size_t)total * 12, cudaMemcpyHostToDevice, s));
+    if (want_vel) CUDA_TRY(cudaMemcpyAsync(pa.hvel, cvel, (size_t)total * 12, cudaMemcpyHostToDevice, s));
+    launch_pack(pa, 1, s);
+    CUDA_TRY(cudaGetLastError());
+    return PBDR_OK;
+  }
+  launch_pack(pa, 0, s);
+  if (want_pos) CUDA_TRY(cudaMemcpyAsync(hpos, pa.hpos, (size_t)total * 12, cudaMemcpyDeviceToHost, s));
+  if (want_vel) CUDA_TRY(cudaMemcpyAsync(hvel, pa.hvel, (size_t)total * 12, cudaMemcpyDeviceToHost, s));
+  if (err_bits) {
+    if ((rc = dev_alloc(c, c->err_ids, (size_t)n * 4))) return rc;
+    if ((rc = dev_alloc(c, c->err_out, (size_t)n * 4))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(c->err_ids.p, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    k_errs<<<(n + 255) / 256, 256, 0, s>>>(c->scene_err.as<uint32_t>(), c->err_ids.as<int32_t>(), n,
+                                            c->err_out.as<uint32_t>());
+    CUDA_TRY(cudaMemcpyAsync(err_bits, c->err_out.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PBDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pbdr_last_error(void) { return g_err.c_str(); }
+
+int pbdr_ctx_create(int device, size_t hbm_budget_bytes, pbdr_ctx **out) {
+  g_err.clear();
+  if (!out) return fail(PBDR_ERR_INVALID, "NULL out");
+  *out = nullptr;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(PBDR_ERR_INVALID, "no CUDA device " + std::to_string(device));
+  CUDA_TRY(cudaSetDevice(device));
+  auto *c = new (std::nothrow) pbdr_ctx();
+  if (!c) return fail(PBDR_ERR_OOM, "host allocation failed");
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  return PBDR_OK;
+}
+
+int pbdr_ctx_destroy(pbdr_ctx *c) {
+  g_err.clear();
+  if (!c) return PBDR_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  invalidate_plans(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return PBDR_OK;
+}
+
+int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
+  g_err.clear();
+  if (!c || !d || !out) return fail(PBDR_ERR_INVALID, "NULL argument");
+  const int32_t N = d->num_particles, B = d->num_bodies;
+  if (N < 0 || B < 0) return fail(PBDR_ERR_INVALID, "negative particle or body count");
+  if ((N == 0) != (B == 0)) return fail(PBDR_ERR_INVALID, "a scene with particles needs bodies and vice versa");
+  if (N > 0 && (!d->pos || !d->vel || !d->inv_mass || !d->body_off))
+    return fail(PBDR_ERR_INVALID, "NULL array in descriptor");
+  if (!(d->radius > 0.f) || !std::isfinite(d->radius)) return fail(PBDR_ERR_INVALID, "radius must be > 0");
+  if (!(d->friction >= 0.f) || !std::isfinite(d->friction)) return fail(PBDR_ERR_INVALID, "friction must be >= 0");
+  if (!(d->dt > 0.f) || !std::isfinite(d->dt)) return fail(PBDR_ERR_INVALID, "dt must be > 0");
+  if (d->iterations < 1 || d->iterations > 1024) return fail(PBDR_ERR_INVALID, "iterations must be in 1..1024");
+  if (!finite3(d->gravity) || !finite3(d->plane) || !std::isfinite(d->plane[3]))
+    return fail(PBDR_ERR_INVALID, "gravity and plane must be finite");
+  const uint32_t known = PBDR_STD_VELOCITY | PBDR_NO_LINMOM | PBDR_NO_ANGMOM | PBDR_CONTACT_AVG | PBDR_SM_FROM_XI;
+  if (d->flags & ~known) return fail(PBDR_ERR_INVALID, "unknown flag bits");
+  if (d->flags & PBDR_SM_FROM_XI) return fail(PBDR_ERR_UNSUPPORTED, "PBDR_SM_FROM_XI is not implemented on the GPU path");
+  const double nl = std::sqrt((double)d->plane[0] * d->plane[0] + (double)d->plane[1] * d->plane[1] +
+                              (double)d->plane[2] * d->plane[2]);
+  if (!(std::fabs(nl - 1.0) < 1e-3)) return fail(PBDR_ERR_INVALID, "plane normal must be unit length");
+  if (N > 0) {
+    if (d->body_off[0] != 0 || d->body_off[B] != N) return fail(PBDR_ERR_INVALID, "body_off must start at 0 and end at N");
+    for (int32_t b = 0; b < B; ++b) {
+      const int32_t cnt = d->body_off[b + 1] - d->body_off[b];
+      if (cnt <= 0) return fail(PBDR_ERR_INVALID, "body_off must be strictly increasing");
+      if (cnt > kMaxBodyParticles) return fail(PBDR_ERR_INVALID, "body too large");
+    }
+    for (int32_t p = 0; p < N; ++p) {
+      if (!(d->inv_mass[p] > 0.f) || !std::isfinite(d->inv_mass[p]))
+        return fail(PBDR_ERR_INVALID, "inverse masses must be finite and > 0");
+      if (!finite3(d->pos + 3 * p) || !finite3(d->vel + 3 * p))
+        return fail(PBDR_ERR_INVALID, "positions and velocities must be finite");
+    }
+  }
+  if ((int64_t)c->np_used + N > INT32_MAX / 2 || (int64_t)c->nb_used + B > INT32_MAX / 2)
+    return fail(PBDR_ERR_INVALID, "context particle or body count overflow");
+  const int32_t sid = (int32_t)c->sh.size();
+  const int32_t old_pcap = c->pcap;
+  int rc = ensure_capacity(c, c->np_used + N, c->nb_used + B, sid + 1);
+  if (rc) return rc;
+  if (c->pcap != old_pcap) invalidate_plans(c);
+
+  // host-side FP64 rest shape (Mueller et al. 2005): M, c0, q = x0 - c0
+  std::vector<float4> X(N), V(N), Q(N);
+  std::vector<int32_t> pb(N);
+  std::vector<BodyRec> br(B);
+  std::vector<float4> com(B);
+  for (int32_t b = 0; b < B; ++b) {
+    const int32_t s0 = d->body_off[b], s1 = d->body_off[b + 1];
+    double M = 0, cx = 0, cy = 0, cz = 0;
+    for (int32_t p = s0; p < s1; ++p) {
+      const double m = 1.0 / (double)d->inv_mass[p];
+      M += m;
+      cx += m * d->pos[3 * p];
+      cy += m * d->pos[3 * p + 1];
+      cz += m * d->pos[3 * p + 2];
+    }
+    cx /= M;
+    cy /= M;
+    cz /= M;
+    com[b] = make_float4((float)cx, (float)cy, (float)cz, 0.f);
+    double qs[3] = {0, 0, 0};
+    for (int32_t p = s0; p < s1; ++p) {
+      const float m = (float)(1.0 / (double)d->inv_mass[p]);
+      float4 q = make_float4((float)(d->pos[3 * p] - cx), (float)(d->pos[3 * p + 1] - cy),
+                             (float)(d->pos[3 * p + 2] - cz), m);
+      Q[p] = q;
+      const double md = 1.0 / (double)d->inv_mass[p];
+      qs[0] += md * q.x;
+      qs[1] += md * q.y;
+      qs[2] += md * q.z;
+      X[p] = make_float4(d->pos[3 * p], d->pos[3 * p + 1], d->pos[3 * p + 2], d->inv_mass[p]);
+      V[p] = make_float4(d->vel[3 * p], d->vel[3 * p + 1], d->vel[3 * p + 2], 0.f);
+      pb[p] = c->nb_used + b;
+    }
+    BodyRec &r = br[b];
+    r.start = c->np_used + s0;
+    r.count = s1 - s0;
+    r.scene = sid;
+    r.has_wrench = 0;
+    r.mass = (float)M;
+    r.inv_mass = (float)(1.0 / M);
+    r.qsx = (float)qs[0];
+    r.qsy = (float)qs[1];
+    r.qsz = (float)qs[2];
+  }
+  SceneHost S;
+  S.alive = true;
+  S.p0 = c->np_used;
+  S.np = N;
+  S.b0 = c->nb_used;
+  S.nb = B;
+  ScenePar &P = S.par;
+  P.radius = d->radius;
+  P.friction = d->friction;
+  P.dt = d->dt;
+  P.inv_dt = (float)(1.0 / (double)d->dt);
+  P.gx = d->gravity[0];
+  P.gy = d->gravity[1];
+  P.gz = d->gravity[2];
+  P.nx = (float)(d->plane[0] / nl);
+  P.ny = (float)(d->plane[1] / nl);
+  P.nz = (float)(d->plane[2] / nl);
+  P.nd = d->plane[3];
+  {  // neighbour-grid constants (FP32): Rn = 2.2 r, cell h = Rn (1 + 2^-10)
+    const float Rn = (float)(2.2 * (double)d->radius);
+    const float h = (float)((double)Rn * (1.0 + 1.0 / 1024.0));
+    volatile float rr = Rn * Rn;
+    P.Rn2 = rr;
+    P.inv_h = (float)(1.0 / (double)h);
+  }
+  P.iterations = d->iterations;
+  P.flags = d->flags;
+  P.T = table_size(N);
+  P.p0 = S.p0;
+  P.np = N;
+  P.b0 = S.b0;
+  P.nb = B;
+  std::vector<float4> quat(B, make_float4(0.f, 0.f, 0.f, 1.f));
+  std::vector<BodyWrench> wr(B);
+  std::memset(wr.data(), 0, sizeof(BodyWrench) * (size_t)B);
+  if (N > 0) {
+    CUDA_TRY(cudaMemcpy(c->X[0].as<float4>() + S.p0, X.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->V[0].as<float4>() + S.p0, V.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->Q.as<float4>() + S.p0, Q.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->pbody.as<int32_t>() + S.p0, pb.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->bodies.as<BodyRec>() + S.b0, br.data(), (size_t)B * sizeof(BodyRec), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->quat.as<float4>() + S.b0, quat.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->bcom.as<float4>() + S.b0, com.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + S.b0, wr.data(), (size_t)B * sizeof(BodyWrench), cudaMemcpyHostToDevice));
+  }
+  CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
+  c->bh.insert(c->bh.end(), br.begin(), br.end());
+  c->wh.insert(c->wh.end(), wr.begin(), wr.end());
+  c->sh.push_back(S);
+  c->np_used += N;
+  c->nb_used += B;
+  // plans hold per-scene tables sized by the scene count
+  invalidate_plans(c);
+  *out = sid;
+  return PBDR_OK;
+}
+
+int pbdr_destroy_scene(pbdr_ctx *c, pbdr_scene s) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  c->sh[s].alive = false;
+  invalidate_plans(c);
+  return PBDR_OK;
+}
+
+int pbdr_set_body_wrench(pbdr_ctx *c, pbdr_scene s, int32_t body, const float F[3], const float tau[3]) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  SceneHost &S = c->sh[s];
+  if (body < 0 || body >= S.nb) return fail(PBDR_ERR_INVALID, "body index out of range");
+  if (!F || !tau || !finite3(F) || !finite3(tau)) return fail(PBDR_ERR_INVALID, "force and torque must be finite");
+  const int32_t gb = S.b0 + body;
+  const bool on = F[0] != 0.f || F[1] != 0.f || F[2] != 0.f || tau[0] != 0.f || tau[1] != 0.f || tau[2] != 0.f;
+  BodyWrench &w = c->wh[gb];
+  w.force = make_float4(F[0], F[1], F[2], 0.f);
+  w.torque = make_float4(tau[0], tau[1], tau[2], 0.f);
+  const int was = c->bh[gb].has_wrench;
+  c->bh[gb].has_wrench = on ? 1 : 0;
+  S.wrench_bodies += (on ? 1 : 0) - was;
+  CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + gb, &w, sizeof(BodyWrench), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->bodies.as<BodyRec>() + gb, &c->bh[gb], sizeof(BodyRec), cudaMemcpyHostToDevice));
+  if (was != c->bh[gb].has_wrench) invalidate_plans(c);
+  return PBDR_OK;
+}
+
+int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, void *stream) {
+  g_err.clear();
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  if (substeps < 0) return fail(PBDR_ERR_INVALID, "substeps must be >= 0");
+  Plan *P = nullptr;
+  int rc = build_plan(c, ids, n, &P);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t launches = 0;
+  for (int32_t k = 0; k < substeps; ++k) {
+    rc = substep(c, *P, s, launches);
+    if (rc) return rc;
+  }
+  c->last_launches = launches;
+  return PBDR_OK;
+}
+
+int pbdr_read_state(pbdr_ctx *c, pbdr_scene s, float *pos, float *vel, uint32_t *err_bits, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (c->sh[s].np == 0) {
+    if (err_bits) {
+      CUDA_TRY(cudaMemcpy(err_bits, c->scene_err.as<uint32_t>() + s, 4, cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + s, 0, 4));
+    }
+    return PBDR_OK;
+  }
+  return transfer_states(c, &s, 1, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
+}
+
+int pbdr_write_state(pbdr_ctx *c, pbdr_scene s, const float *pos, const float *vel, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (c->sh[s].np == 0) return PBDR_OK;
+  return transfer_states(c, &s, 1, nullptr, nullptr, pos, vel, nullptr, 1, (cudaStream_t)stream);
+}
+
+int pbdr_read_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *pos, float *vel,
+                     uint32_t *err_bits, void *stream) {
+  g_err.clear();
+  return transfer_states(c, ids, n, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
+}
+
+int pbdr_write_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, const float *pos, const float *vel,
+                      void *stream) {
+  g_err.clear();
+  return transfer_states(c, ids, n, nullptr, nullptr, pos, vel, nullptr, 1, (cudaStream_t)stream);
+}
+
+int pbdr_scene_info(pbdr_ctx *c, pbdr_scene s, int32_t *np, int32_t *nb) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (np) *np = c->sh[s].np;
+  if (nb) *nb = c->sh[s].nb;
+  return PBDR_OK;
+}
+
+int pbdr_build_neighbors(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, void *stream) {
+  g_err.clear();
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  Plan *P = nullptr;
+  int rc = build_plan(c, ids, n, &P);
+  if (rc) return rc;
+  if (P->np == 0) return PBDR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t launches = 0;
+  float4 *X0 = c->X[0].as<float4>();
+  launches += launch_predict(predict_args(c, *P, X0, c->V[0].as<float4>(), X0, c->V[0].as<float4>(), 0), s);
+  rc = neighbor_stage(c, *P, X0, s, launches);
+  if (rc) return rc;
+  CUDA_TRY(cudaGetLastError());
+  c->last_launches = launches;
+  return PBDR_OK;
+}
+
+int pbdr_read_neighbors(pbdr_ctx *c, pbdr_scene s, uint32_t *sorted_key, uint32_t *sorted_id, int32_t *off,
+                        int32_t *idx, int64_t idx_cap, int64_t *idx_count, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (!idx_count) return fail(PBDR_ERR_INVALID, "NULL idx_count");
+  Plan *P = c->last_nbr_plan;
+  if (!P) return fail(PBDR_ERR_INVALID, "no neighbour stage has run since the last scene change");
+  int pos_in_plan = -1;
+  for (size_t i = 0; i < P->ids.size(); ++i)
+    if (P->ids[i] == s) pos_in_plan = (int)i;
+  if (pos_in_plan < 0) return fail(PBDR_ERR_INVALID, "scene was not part of the last neighbour stage");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaStreamSynchronize(st));
+  const SceneHost &S = c->sh[s];
+  const int32_t N = S.np;
+  const int64_t so = P->seg_off[pos_in_plan];
+  const uint32_t hb = P->hbase_host[s];
+  std::vector<uint32_t> k(N), v(N);
+  if (N > 0) {
+    const uint32_t *sk = P->sorted_in_b ? P->keys_b.as<uint32_t>() : P->keys_a.as<uint32_t>();
+    const uint32_t *sv = P->sorted_in_b ? P->vals_b.as<uint32_t>() : P->vals_a.as<uint32_t>();
+    CUDA_TRY(cudaMemcpy(k.data(), sk + so, (size_t)N * 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(v.data(), sv + so, (size_t)N * 4, cudaMemcpyDeviceToHost));
+  }
+  for (int32_t i = 0; i < N; ++i) {
+    if (sorted_key) sorted_key[i] = k[i] - hb;
+    if (sorted_id) sorted_id[i] = v[i] - (uint32_t)S.p0;
+  }
+  std::vector<int32_t> cnt(N);
+  if (N > 0) CUDA_TRY(cudaMemcpy(cnt.data(), c->nbr_cnt.as<int32_t>() + S.p0, (size_t)N * 4, cudaMemcpyDeviceToHost));
+  int32_t maxc = 0;
+  int64_t total = 0;
+  for (int32_t i = 0; i < N; ++i) {
+    maxc = std::max(maxc, cnt[i]);
+    total += cnt[i];
+  }
+  *idx_count = total;
+  if (off) {
+    off[0] = 0;
+    for (int32_t i = 0; i < N; ++i) off[i + 1] = off[i] + cnt[i];
+  }
+  if (idx && total > 0) {
+    std::vector<int32_t> col((size_t)N);
+    std::vector<int64_t> at(N + 1, 0);
+    for (int32_t i = 0; i < N; ++i) at[i + 1] = at[i] + cnt[i];
+    for (int32_t j = 0; j < maxc; ++j) {
+      CUDA_TRY(cudaMemcpy(col.data(), c->nbr.as<int32_t>() + (int64_t)j * c->pcap + S.p0, (size_t)N * 4,
+                          cudaMemcpyDeviceToHost));
+      for (int32_t i = 0; i < N; ++i)
+        if (j < cnt[i] && at[i] + j < idx_cap) idx[at[i] + j] = col[i] - S.p0;
+    }
+  }
+  return PBDR_OK;
+}
+
+int pbdr_neighbor_total(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int64_t *total, void *stream) {
+  g_err.clear();
+  if (!c || !ids || !total || n < 1) return fail(PBDR_ERR_INVALID, "NULL argument");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int64_t t = 0;
+  std::vector<int32_t> cnt;
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = check_scene(c, ids[i]);
+    if (rc) return rc;
+    const SceneHost &S = c->sh[ids[i]];
+    cnt.resize((size_t)S.np);
+    if (S.np) CUDA_TRY(cudaMemcpy(cnt.data(), c->nbr_cnt.as<int32_t>() + S.p0, (size_t)S.np * 4, cudaMemcpyDeviceToHost));
+    for (int32_t k = 0; k < S.np; ++k) t += cnt[k];
+  }
+  *total = t;
+  return PBDR_OK;
+}
+
+int pbdr_set_profiling(pbdr_ctx *c, int enable) {
+  g_err.clear();
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  c->profiling = enable != 0;
+  return PBDR_OK;
+}
+
+int pbdr_read_profile(pbdr_ctx *c, double *stage_ms, int64_t *stage_launches, int32_t nstages) {
+  g_err.clear();
+  if (!c || nstages < 0 || nstages > PBDR_NUM_STAGES) return fail(PBDR_ERR_INVALID, "bad argument");
+  for (const auto &m : c->marks) {
+    CUDA_TRY(cudaEventSynchronize(c->ev_pool[m.e1]));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_pool[m.e0], c->ev_pool[m.e1]));
+    c->stage_ms[m.stage] += ms;
+    c->stage_launches[m.stage] += m.launches;
+  }
+  c->marks.clear();
+  c->ev_used = 0;
+  for (int32_t k = 0; k < nstages; ++k) {
+    if (stage_ms) stage_ms[k] = c->stage_ms[k];
+    if (stage_launches) stage_launches[k] = c->stage_launches[k];
+  }
+  for (int k = 0; k < PBDR_NUM_STAGES; ++k) {
+    c->stage_ms[k] = 0.0;
+    c->stage_launches[k] = 0;
+  }
+  return PBDR_OK;
+}
+
+int pbdr_last_launch_count(pbdr_ctx *c, int64_t *launches) {
+  g_err.clear();
+  if (!c || !launches) return fail(PBDR_ERR_INVALID, "NULL argument");
+  *launches = c->last_launches;
+  return PBDR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Internal declarations of the PBD-R sm_103a library: device-side records,
+// kernel argument blocks and the host launchers each .cu file exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pbdr.h"
+
+namespace pbdr {
+
+// scene flags used by the kernels (same bits as PBDR_* in pbdr.h)
+constexpr uint32_t kStdVelocity = PBDR_STD_VELOCITY;
+constexpr uint32_t kNoLinMom = PBDR_NO_LINMOM;
+constexpr uint32_t kNoAngMom = PBDR_NO_ANGMOM;
+constexpr uint32_t kContactAvg = PBDR_CONTACT_AVG;
+constexpr uint32_t kSmFromXi = PBDR_SM_FROM_XI;
+
+constexpr uint32_t kEmptyCell = 0xFFFFFFFFu;
+constexpr int kMaxBodyParticles = 1 << 20;
+
+// Per-scene constants, read by every kernel (one 80-byte record per scene).
+struct alignas(16) ScenePar {
+  float radius, friction, dt, inv_dt;
+  float gx, gy, gz, Rn2;        // gravity; squared neighbour radius (FP32)
+  float nx, ny, nz, nd;         // ground plane n.x = d
+  float inv_h;                  // inverse cell size of the neighbour grid
+  int32_t iterations;
+  uint32_t flags;
+  uint32_t T;                   // hash-table size (power of two)
+  int32_t p0, np, b0, nb;       // global particle and body ranges
+};
+
+// Per-body constants.
+struct alignas(16) BodyRec {
+  int32_t start, count, scene, has_wrench;
+  float mass, inv_mass, pad0, pad1;
+  float qsx, qsy, qsz, pad2;    // sum_p m_p q_p (FP32 rest offsets; ~0)
+};
+
+// Per-body external wrench, set by the host (force, torque) and the
+// per-substep derived accelerations (aF = F/M, alpha = I^-1 tau about c).
+struct alignas(16) BodyWrench {
+  float4 force;    // xyz
+  float4 torque;   // xyz
+  float4 aF;       // xyz: F/M
+  float4 alpha;    // xyz: I^-1 tau
+  float4 com;      // xyz: c at the start of the substep
+};
+
+// ---- kernel argument blocks ---------------------------------------------
+
+struct PredictArgs {
+  const float4 *X0, *V0;   // state at the start of the substep
+  float4 *Xp, *Vp;         // predicted state (may alias X0/V0)
+  float4 *Xinit;           // X_init copy, or nullptr
+  const int32_t *pbody;
+  const BodyRec *bodies;
+  const ScenePar *scenes;
+  const BodyWrench *wrench;
+  const int32_t *pmap;     // plan particle -> global particle (nullptr: pbase + i)
+  int32_t pbase, np;
+  const uint32_t *hbase;   // scene -> first key of its hash range in this plan
+  uint32_t *keys, *vals;   // cell key and global particle id per plan particle
+  int predict;             // 0: keys of the current positions only
+};
+
+struct CellArgs {
+  const uint32_t *skeys, *svals;
+  const float4 *Xp;
+  const int32_t *pbody;
+  uint32_t *cstart, *cend;
+  float4 *spos;            // sorted (x, y, z, body id bits)
+  int32_t np;
+};
+
+struct NbrArgs {
+  const uint32_t *skeys, *svals;
+  const float4 *spos;
+  const float4 *Xp;        // predicted positions (caller order)
+  const int32_t *pbody;
+  const int32_t *pmap;     // plan particle -> global particle (nullptr: pbase + i)
+  int32_t pbase;
+  const uint32_t *cstart, *cend;
+  const BodyRec *bodies;
+  const ScenePar *scenes;
+  const uint32_t *hbase;
+  int32_t *nbr_cnt;        // [global particle]
+  int32_t *nbr;            // [slot * nbr_stride + global particle]
+  int64_t nbr_stride;
+  int32_t cap;
+  uint32_t *scene_err;
+  int32_t np;
+};
+
+struct IterArgs {
+  const float4 *Xin, *Vin;
+  float4 *Xout, *Vout;
+  const float4 *Q;         // rest offset xyz, particle mass w
+  const float4 *Xinit;     // for PBDR_STD_VELOCITY, else nullptr
+  const int32_t *nbr_cnt, *nbr;
+  int64_t nbr_stride;
+  const BodyRec *bodies;
+  const ScenePar *scenes;
+  float4 *quat;            // per-body rotation (warm start), updated
+  float4 *bcom;            // per-body centre of mass after the last iteration, updated
+  const int32_t *bmap;     // plan body -> global body (nullptr: bbase + i)
+  int32_t bbase, nbodies;
+  uint32_t *scene_err;
+  int32_t k;               // iteration index
+};
+
+struct WrenchArgs {
+  const float4 *X, *Q;
+  const BodyRec *bodies;
+  BodyWrench *wrench;
+  const int32_t *blist;
+  int32_t nb;
+};
+
+struct PackArgs {
+  float4 *X, *V;           // device state
+  float *hpos, *hvel;      // packed xyz staging (device)
+  const int32_t *seg_p0;   // per segment: first global particle
+  const int64_t *seg_off;  // per segment: first packed particle (n+1 entries)
+  int32_t nseg;
+  int64_t total;
+};
+
+// ---- launchers (return the number of kernel launches issued) -------------
+
+int launch_predict(const PredictArgs &a, cudaStream_t s);
+int launch_cells(const CellArgs &a, cudaStream_t s);
+int launch_neighbors(const NbrArgs &a, cudaStream_t s);
+int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
+int launch_wrench(const WrenchArgs &a, cudaStream_t s);
+int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs, keys < 2^bits.  Buffers:
+// ka/va hold the input; kb/vb are scratch of the same size; hist holds
+// radix_hist_words(n) words.  The sorted result ends in (ka, va) when the
+// number of 8-bit passes is even, else in (kb, vb); *out_in_b tells which.
+size_t radix_hist_words(int64_t n);
+int radix_sort_pairs(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb,
+                     uint32_t *hist, int64_t n, int bits, int *out_in_b,
+                     cudaStream_t s);
+
+}  // namespace pbdr

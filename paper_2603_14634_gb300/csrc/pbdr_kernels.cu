@@ -1,0 +1,663 @@
+// PBD-R substep kernels for sm_103a.
+//
+// Data layout (all FP32, float4 SoA, one slot per particle in caller order):
+//   X  = (x, y, z, w)        position and inverse mass w_p
+//   V  = (vx, vy, vz, 0)     velocity
+//   Q  = (qx, qy, qz, m)     rest offset q_p = x0_p - c0 and mass m_p
+// Bodies are contiguous particle ranges; scenes are contiguous body ranges.
+//
+// Kernels of one substep (Algorithm 1):
+//   k_predict   integration (l.1-4) and the hashed-grid cell key of x~
+//   (radix sort of (key, particle))
+//   k_cells     bucket [start, end) ranges and positions in sorted order
+//   k_neighbors candidate lists N(p) with the exact FP32 predicate (ELL)
+//   k_iterate   one solver iteration (l.5-10) for one body per warp:
+//               contacts -> X_bsm, V_bsm; shape matching -> X_asm, V_asm;
+//               momentum enforcement -> X_{i+1}, V_{i+1}
+#include <math.h>
+
+#include "pbdr_internal.cuh"
+
+namespace pbdr {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) {
+  return make_float3(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) {
+  return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float3 operator*(float s, float3 a) {
+  return make_float3(s * a.x, s * a.y, s * a.z);
+}
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// ---- hashed uniform grid (FP32, round-to-nearest, no contraction) --------
+
+__device__ __forceinline__ int32_t cell_coord(float x, float inv_h) {
+  float u = floorf(__fmul_rn(x, inv_h));
+  u = fminf(fmaxf(u, -1.0e9f), 1.0e9f);
+  return (int32_t)u;
+}
+
+// Teschner et al. 2003 spatial hash of integer cell coordinates
+__device__ __forceinline__ uint32_t cell_hash(int32_t ix, int32_t iy, int32_t iz) {
+  return ((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u);
+}
+
+// squared distance, dx = x_q - x_p per axis, (dx^2 + dy^2) + dz^2, each op RN
+__device__ __forceinline__ float d2_rn(float4 p, float4 q) {
+  float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y), dz = __fsub_rn(q.z, p.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// ---------------------------------------------------------------------------
+// integration step + cell keys
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_predict(PredictArgs a) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
+  const int32_t b = a.pbody[p];
+  const BodyRec br = a.bodies[b];
+  const ScenePar sp = a.scenes[br.scene];
+  float4 x = a.X0[p];
+  if (a.predict) {
+    const float4 v = a.V0[p];
+    float3 acc = make_float3(sp.gx, sp.gy, sp.gz);
+    if (br.has_wrench) {
+      const BodyWrench wr = a.wrench[b];
+      float3 r = f3(x) - f3(wr.com);
+      acc = acc + f3(wr.aF) + cross(f3(wr.alpha), r);
+    }
+    // v~ = v + dt w f_ext ;  x~ = x_init + dt v~
+    float3 vt = f3(v) + sp.dt * acc;
+    float3 xt = f3(x) + sp.dt * vt;
+    if (a.Xinit) a.Xinit[p] = x;
+    x = make_float4(xt.x, xt.y, xt.z, x.w);
+    a.Xp[p] = x;
+    a.Vp[p] = make_float4(vt.x, vt.y, vt.z, 0.f);
+  }
+  const uint32_t h = cell_hash(cell_coord(x.x, sp.inv_h), cell_coord(x.y, sp.inv_h),
+                               cell_coord(x.z, sp.inv_h));
+  a.keys[i] = a.hbase[br.scene] + (h & (sp.T - 1u));
+  a.vals[i] = (uint32_t)p;
+}
+
+// ---------------------------------------------------------------------------
+// bucket ranges of the sorted keys + positions gathered in sorted order
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_cells(CellArgs a) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  const uint32_t key = a.skeys[i];
+  if (i == 0 || a.skeys[i - 1] != key) a.cstart[key] = (uint32_t)i;
+  if (i == a.np - 1 || a.skeys[i + 1] != key) a.cend[key] = (uint32_t)(i + 1);
+  const uint32_t p = a.svals[i];
+  const float4 x = a.Xp[p];
+  a.spos[i] = make_float4(x.x, x.y, x.z, __int_as_float(a.pbody[p]));
+}
+
+// ---------------------------------------------------------------------------
+// neighbour lists: N(p) = {q : body(q) != body(p), d2_rn(p, q) < Rn^2},
+// ascending, stored column-major (slot j of particle p at j*stride + p)
+// ---------------------------------------------------------------------------
+
+constexpr int kNbrCapMax = 64;
+
+__global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
+  // threads walk the particles in caller order: the particles of a body are
+  // contiguous and close in space, so a warp's bucket lookups coincide
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
+  const float4 xp = a.Xp[p];
+  const int32_t bp = a.pbody[p];
+  const int32_t s = a.bodies[bp].scene;
+  const ScenePar sp = a.scenes[s];
+  const uint32_t hb = a.hbase[s], mask = sp.T - 1u;
+  const int32_t ix = cell_coord(xp.x, sp.inv_h), iy = cell_coord(xp.y, sp.inv_h),
+                iz = cell_coord(xp.z, sp.inv_h);
+  int32_t list[kNbrCapMax];
+  const int cap = a.cap;
+  int cnt = 0;
+  // each of the 27 cells once; a bucket shared by several cells (hash
+  // collision) is scanned once per cell and only that cell's particles are
+  // taken, so no candidate appears twice
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int32_t cx = ix + dx, cy = iy + dy, cz = iz + dz;
+        const uint32_t bkt = hb + (cell_hash(cx, cy, cz) & mask);
+        const uint32_t st = a.cstart[bkt];
+        if (st == kEmptyCell) continue;
+        const uint32_t en = a.cend[bkt];
+        for (uint32_t j = st; j < en; ++j) {
+          const float4 xq = a.spos[j];
+          if (__float_as_int(xq.w) == bp) continue;
+          if (cell_coord(xq.x, sp.inv_h) != cx || cell_coord(xq.y, sp.inv_h) != cy ||
+              cell_coord(xq.z, sp.inv_h) != cz)
+            continue;
+          if (!(d2_rn(xp, xq) < sp.Rn2)) continue;
+          const int32_t q = (int32_t)a.svals[j];
+          if (cnt < cap) {
+            int at = cnt;   // insertion into the ascending list
+            while (at > 0 && list[at - 1] > q) {
+              list[at] = list[at - 1];
+              --at;
+            }
+            list[at] = q;
+          }
+          ++cnt;
+        }
+      }
+  const int nw = cnt < cap ? cnt : cap;
+  for (int k = 0; k < nw; ++k) a.nbr[(int64_t)k * a.nbr_stride + p] = list[k];
+  a.nbr_cnt[p] = nw;
+  if (cnt > cap) atomicOr(&a.scene_err[s], (uint32_t)PBDR_EBIT_NBR_OVERFLOW);
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 helpers for the per-body solves (every lane computes the same values)
+// ---------------------------------------------------------------------------
+
+struct Mat3 {
+  float m[9];   // row-major
+};
+
+__device__ __forceinline__ void quat_to_mat(float4 q, float *R) {
+  // q = (x, y, z, w), unit
+  const float x = q.x, y = q.y, z = q.z, w = q.w;
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - z * w);
+  R[2] = 2.f * (x * z + y * w);
+  R[3] = 2.f * (x * y + z * w);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - x * w);
+  R[6] = 2.f * (x * z - y * w);
+  R[7] = 2.f * (y * z + x * w);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// solve the symmetric system S u = g (S = [s00 s01 s02; . s11 s12; . . s22]);
+// returns false if S is not positive definite (leading minors) or singular
+__device__ __forceinline__ bool solve_spd3(float s00, float s01, float s02, float s11, float s12,
+                                           float s22, float3 g, float3 &u, float rel_tol) {
+  const float c00 = s11 * s22 - s12 * s12;
+  const float c01 = s02 * s12 - s01 * s22;
+  const float c02 = s01 * s12 - s02 * s11;
+  const float det = s00 * c00 + s01 * c01 + s02 * c02;
+  const float tr = (s00 + s11 + s22) * (1.f / 3.f);
+  if (!(s00 > 0.f) || !(s00 * s11 - s01 * s01 > 0.f) || !(det > rel_tol * tr * tr * tr)) {
+    u = make_float3(0.f, 0.f, 0.f);
+    return false;
+  }
+  const float c11 = s00 * s22 - s02 * s02;
+  const float c12 = s01 * s02 - s00 * s12;
+  const float c22 = s00 * s11 - s01 * s01;
+  const float id = 1.f / det;
+  u.x = (c00 * g.x + c01 * g.y + c02 * g.z) * id;
+  u.y = (c01 * g.x + c11 * g.y + c12 * g.z) * id;
+  u.z = (c02 * g.x + c12 * g.y + c22 * g.z) * id;
+  return true;
+}
+
+// unit quaternion (x, y, z, w) of a rotation matrix (Shepperd's method:
+// branch on the largest of the trace and the diagonal)
+__device__ __forceinline__ float4 mat_to_quat(const float *R) {
+  const float tr = R[0] + R[4] + R[8];
+  float4 q;
+  if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + tr, 1e-30f));
+    q = make_float4((R[7] - R[5]) / s, (R[2] - R[6]) / s, (R[3] - R[1]) / s, 0.25f * s);
+  } else if (R[0] >= R[4] && R[0] >= R[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[0] - R[4] - R[8], 1e-30f));
+    q = make_float4(0.25f * s, (R[1] + R[3]) / s, (R[2] + R[6]) / s, (R[7] - R[5]) / s);
+  } else if (R[4] >= R[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[4] - R[0] - R[8], 1e-30f));
+    q = make_float4((R[1] + R[3]) / s, 0.25f * s, (R[5] + R[7]) / s, (R[2] - R[6]) / s);
+  } else {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[8] - R[0] - R[4], 1e-30f));
+    q = make_float4((R[2] + R[6]) / s, (R[5] + R[7]) / s, 0.25f * s, (R[3] - R[1]) / s);
+  }
+  const float n = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  return make_float4(q.x * n, q.y * n, q.z * n, q.w * n);
+}
+
+// Orthogonal polar factor of a nonsingular A by Higham's scaled Newton
+// iteration X <- (g X + (g X)^-T)/2, g = (|X^-1|_F / |X|_F)^(1/2).
+// Returns false if A is (nearly) singular or the factor is a reflection.
+__device__ bool polar_higham(const float *A, float *U) {
+  float X[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) X[k] = A[k];
+  for (int it = 0; it < 24; ++it) {
+    // cofactors C_ij: X^-T = C / det
+    const float c0 = X[4] * X[8] - X[5] * X[7], c1 = X[5] * X[6] - X[3] * X[8],
+                c2 = X[3] * X[7] - X[4] * X[6], c3 = X[2] * X[7] - X[1] * X[8],
+                c4 = X[0] * X[8] - X[2] * X[6], c5 = X[1] * X[6] - X[0] * X[7],
+                c6 = X[1] * X[5] - X[2] * X[4], c7 = X[2] * X[3] - X[0] * X[5],
+                c8 = X[0] * X[4] - X[1] * X[3];
+    const float det = X[0] * c0 + X[1] * c1 + X[2] * c2;
+    float nx = 0.f, nc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nx += X[k] * X[k];
+    const float C[9] = {c0, c1, c2, c3, c4, c5, c6, c7, c8};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
+    if (!(fabsf(det) > 1e-30f) || !(nx > 0.f)) return false;
+    const float ninv = sqrtf(nc) / fabsf(det);   // |X^-1|_F
+    const float g = sqrtf(ninv / sqrtf(nx));
+    const float a = 0.5f * g, b = 0.5f / (g * det);
+    float diff = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float xn = a * X[k] + b * C[k];
+      diff += (xn - X[k]) * (xn - X[k]);
+      X[k] = xn;
+    }
+    if (diff < 1e-12f) break;
+  }
+  const float det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                    X[2] * (X[3] * X[7] - X[4] * X[6]);
+  if (!(det > 0.5f)) return false;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) U[k] = X[k];
+  return true;
+}
+
+// Rotation maximising tr(R^T A) over SO(3) (the rotation of the least-squares
+// rigid fit of shape matching), by Newton steps on SO(3) from the warm start
+// q: with r_i, a_i the columns of R and A, the objective near R is
+// f(th) ~ f + g.th - th^T H th / 2 with g = sum r_i x a_i and
+// H = (sum r_i.a_i) I3 - sym(sum r_i a_i^T), so th = H^-1 g.  If H is not
+// positive definite at the warm start (the start is far from the optimum),
+// the start is replaced by the polar factor from Higham's iteration; where
+// that fails too (singular or inverted A) damped gradient steps are taken.
+__device__ float4 polar_rotation(const float *A, float4 q) {
+  bool restarted = false;
+  for (int it = 0; it < 8; ++it) {
+    float R[9];
+    quat_to_mat(q, R);
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    float M[9];
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float3 r = make_float3(R[i], R[3 + i], R[6 + i]);
+      const float3 av = make_float3(A[i], A[3 + i], A[6 + i]);
+      g = g + cross(r, av);
+      t += dot(r, av);
+    }
+    // sum_i r_i a_i^T = R A^T
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        M[3 * r + c] = R[3 * r + 0] * A[3 * c + 0] + R[3 * r + 1] * A[3 * c + 1] +
+                       R[3 * r + 2] * A[3 * c + 2];
+    float3 th;
+    const bool ok = solve_spd3(t - M[0], -0.5f * (M[1] + M[3]), -0.5f * (M[2] + M[6]), t - M[4],
+                               -0.5f * (M[5] + M[7]), t - M[8], g, th, 1e-6f);
+    if (!ok) {
+      float U[9];
+      if (!restarted && polar_higham(A, U)) {
+        restarted = true;
+        q = mat_to_quat(U);
+        continue;
+      }
+      const float gn = sqrtf(dot(g, g));
+      const float den = fabsf(t) + gn + 1e-30f;
+      th = (1.f / den) * g;
+    }
+    const float thn2 = dot(th, th);
+    // q <- normalize(q + (0, th/2) (x) q)
+    const float4 dq = make_float4(0.5f * (th.x * q.w + th.y * q.z - th.z * q.y),
+                                  0.5f * (th.y * q.w + th.z * q.x - th.x * q.z),
+                                  0.5f * (th.z * q.w + th.x * q.y - th.y * q.x),
+                                  -0.5f * (th.x * q.x + th.y * q.y + th.z * q.z));
+    q = make_float4(q.x + dq.x, q.y + dq.y, q.z + dq.z, q.w + dq.w);
+    const float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    q = make_float4(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
+    if (thn2 < 4e-14f) break;   // |th| < 2e-7 rad: at the FP32 noise floor
+  }
+  return q;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// contact corrections of one particle (Sec. III-A constraints (1), (2)):
+// ground push-out by the penetration and pairwise push-out split by inverse
+// mass, each with Coulomb friction removing the tangential displacement of
+// this substep up to mu times the penetration.  The displacement since the
+// start of the substep, x - x_init, equals v dt for every state of the solve
+// (each change of x comes with the same change of v*dt), and is formed as
+// v dt to avoid the cancellation of x - x_init in FP32.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float3 friction_cut(float3 del, float3 n, float mu_pen) {
+  const float dn = dot(del, n);
+  const float3 dt_ = del - dn * n;
+  const float lt = sqrtf(dot(dt_, dt_));
+  if (!(lt > 0.f)) return make_float3(0.f, 0.f, 0.f);
+  const float f = fminf(mu_pen / lt, 1.f);
+  return f * dt_;
+}
+
+__device__ __forceinline__ float3 contact_dx(const IterArgs &a, const ScenePar &sp, int32_t p,
+                                             float4 xp, float4 vp) {
+  const float r = sp.radius, d_c = 2.f * r, mu = sp.friction, dt = sp.dt;
+  const float3 n = make_float3(sp.nx, sp.ny, sp.nz);
+  float3 dX = make_float3(0.f, 0.f, 0.f);
+  // ground
+  const float pen_g = r - (dot(n, f3(xp)) - sp.nd);
+  if (pen_g > 0.f) {
+    const float3 del = dt * f3(vp);
+    dX = pen_g * n - friction_cut(del, n, mu * pen_g);
+  }
+  // particle-particle over the ascending candidate list
+  const int32_t cnt = a.nbr_cnt[p];
+  float3 acc = make_float3(0.f, 0.f, 0.f);
+  int active = 0;
+  for (int32_t j = 0; j < cnt; ++j) {
+    const int32_t q = a.nbr[(int64_t)j * a.nbr_stride + p];
+    const float4 xq = a.Xin[q];
+    const float3 diff = f3(xp) - f3(xq);
+    const float dd = dot(diff, diff);
+    if (dd > 0.f && dd < d_c * d_c) {
+      const float d = sqrtf(dd);
+      const float pen = d_c - d;
+      const float3 nh = (1.f / d) * diff;
+      const float4 vq = a.Vin[q];
+      const float s = xp.w / (xp.w + xq.w);
+      const float3 del = dt * (f3(vp) - f3(vq));
+      acc = acc + s * (pen * nh - friction_cut(del, nh, mu * pen));
+      ++active;
+    }
+  }
+  if ((sp.flags & kContactAvg) && active > 0) acc = (1.f / (float)active) * acc;
+  return dX + acc;
+}
+
+// ---------------------------------------------------------------------------
+// one solver iteration, one body per warp
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.nbodies) return;
+  const int32_t b = a.bmap ? a.bmap[w] : a.bbase + w;
+  const BodyRec br = a.bodies[b];
+  const ScenePar sp = a.scenes[br.scene];
+  const int32_t p0 = br.start, pe = br.start + br.count;
+  if (a.k >= sp.iterations) {   // scene needs fewer iterations: carry the state
+    for (int32_t p = p0 + lane; p < pe; p += 32) {
+      a.Xout[p] = a.Xin[p];
+      a.Vout[p] = a.Vin[p];
+    }
+    return;
+  }
+  const float dt = sp.dt, idt = sp.inv_dt;
+  const bool std_vel = (sp.flags & kStdVelocity) != 0;
+  // anchor of the FP32 body sums: the body's centre of mass after the previous
+  // iteration, so that x - anchor stays within the body's extent
+  const float3 anc = f3(a.bcom[b]);
+
+  // (1) contacts from X_i (Jacobi) -> X_bsm, V_bsm ; first body reduction
+  float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xp = a.Xin[p], vp = a.Vin[p];
+    const float3 dX = contact_dx(a, sp, p, xp, vp);
+    const float3 xb = f3(xp) + dX;
+    float3 vb;
+    if (std_vel)
+      vb = idt * (xb - f3(a.Xinit[p]));
+    else
+      vb = f3(vp) + idt * dX;   // V_i + dX/dt (Sec. III-B)
+    a.Xout[p] = make_float4(xb.x, xb.y, xb.z, xp.w);
+    a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 e = xb - anc;
+    const float3 me = m * e;
+    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
+    sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
+    sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
+    sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
+    sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
+    const float3 l = cross(me, vb);
+    sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sx[k] = warp_sum(sx[k]);
+    sP[k] = warp_sum(sP[k]);
+    sL[k] = warp_sum(sL[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) sA[k] = warp_sum(sA[k]);
+
+  const float iM = br.inv_mass, M = br.mass;
+  const float3 cA = iM * make_float3(sx[0], sx[1], sx[2]);   // c_bsm - anchor
+  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
+  const float3 Lb = make_float3(sL[0], sL[1], sL[2]) - cross(cA, Pb);
+  // A = sum m (x - c) q^T = sum m (x - a) q^T - (c - a) (sum m q)^T
+  float A[9];
+  {
+    const float qs[3] = {br.qsx, br.qsy, br.qsz};
+    const float ca[3] = {cA.x, cA.y, cA.z};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
+  }
+  const float4 qrot = polar_rotation(A, a.quat[b]);
+  float R[9];
+  quat_to_mat(qrot, R);
+
+  // (2) shape-matching goals g = R q + c -> X_asm, V_asm ; second reduction
+  float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f};
+  float sXX[6] = {0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 grel = make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z,
+                                    R[3] * q.x + R[4] * q.y + R[5] * q.z,
+                                    R[6] * q.x + R[7] * q.y + R[8] * q.z) + cA;
+    const float3 dsm = grel - (f3(xb4) - anc);
+    const float3 xa = f3(xb4) + dsm;
+    float3 va;
+    if (std_vel)
+      va = idt * (xa - f3(a.Xinit[p]));
+    else
+      va = f3(vb4) + idt * dsm;
+    a.Xout[p] = make_float4(xa.x, xa.y, xa.z, xb4.w);
+    a.Vout[p] = make_float4(va.x, va.y, va.z, 0.f);
+    const float3 e = xa - anc;
+    const float3 me = m * e;
+    sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
+    sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
+    const float3 l = cross(me, va);
+    sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
+    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
+    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sx2[k] = warp_sum(sx2[k]);
+    sP2[k] = warp_sum(sP2[k]);
+    sL2[k] = warp_sum(sL2[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
+
+  // momentum enforcement (Sec. III-C): dv = (P_bsm - P_asm)/M,
+  // w = I^-1 (L_asm - L_bsm) with I about c_asm
+  const float3 cA2 = iM * make_float3(sx2[0], sx2[1], sx2[2]);   // c_asm - anchor
+  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
+  const float3 La = make_float3(sL2[0], sL2[1], sL2[2]) - cross(cA2, Pa);
+  float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
+  if (!(sp.flags & kNoLinMom)) dv = iM * (Pb - Pa);
+  if (!(sp.flags & kNoAngMom)) {
+    // S = sum m r r^T about c_asm
+    const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
+                s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
+                s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
+    const float tr = s00 + s11 + s22;
+    // I = tr(S) I3 - S
+    solve_spd3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, La - Lb, om, 1e-6f);
+  }
+
+  // (3) apply the uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
+  bool bad = false;
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xa4 = a.Xout[p], va4 = a.Vout[p];
+    const float3 r = (f3(xa4) - anc) - cA2;
+    const float3 corr = dv - cross(om, r);
+    const float3 v = f3(va4) + corr;
+    const float3 x = f3(xa4) + dt * corr;
+    a.Xout[p] = make_float4(x.x, x.y, x.z, xa4.w);
+    a.Vout[p] = make_float4(v.x, v.y, v.z, 0.f);
+    bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
+  }
+  if (lane == 0) {
+    a.quat[b] = qrot;
+    const float3 cn = anc + cA2 + dt * dv;   // CoM after the correction
+    a.bcom[b] = make_float4(cn.x, cn.y, cn.z, 0.f);
+  }
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(&a.scene_err[br.scene], (uint32_t)PBDR_EBIT_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// per-substep wrench accelerations: aF = F/M, alpha = I^-1 tau with c and I
+// of the current positions (one body per warp, anchored FP32 sums)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) k_wrench(WrenchArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.nb) return;
+  const int32_t b = a.blist[w];
+  const BodyRec br = a.bodies[b];
+  const int32_t p0 = br.start, pe = br.start + br.count;
+  const float3 anc = f3(a.X[p0]);
+  float sx[3] = {0.f, 0.f, 0.f}, sXX[6] = {0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float m = a.Q[p].w;
+    const float3 e = f3(a.X[p]) - anc;
+    const float3 me = m * e;
+    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
+    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
+    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sx[k] = warp_sum(sx[k]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
+  if (lane != 0) return;
+  const float M = br.mass, iM = br.inv_mass;
+  const float3 d = iM * make_float3(sx[0], sx[1], sx[2]);
+  const float s00 = sXX[0] - M * d.x * d.x, s01 = sXX[1] - M * d.x * d.y,
+              s02 = sXX[2] - M * d.x * d.z, s11 = sXX[3] - M * d.y * d.y,
+              s12 = sXX[4] - M * d.y * d.z, s22 = sXX[5] - M * d.z * d.z;
+  const float tr = s00 + s11 + s22;
+  BodyWrench wr = a.wrench[b];
+  float3 alpha;
+  solve_spd3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, f3(wr.torque), alpha, 1e-6f);
+  const float3 aF = iM * f3(wr.force);
+  const float3 c = anc + d;
+  wr.aF = make_float4(aF.x, aF.y, aF.z, 0.f);
+  wr.alpha = make_float4(alpha.x, alpha.y, alpha.z, 0.f);
+  wr.com = make_float4(c.x, c.y, c.z, 0.f);
+  a.wrench[b] = wr;
+}
+
+// ---------------------------------------------------------------------------
+// packing between the float4 state and caller xyz arrays (segments = scenes)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_pack(PackArgs a, int unpack) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.total) return;
+  int lo = 0, hi = a.nseg - 1;   // segment of packed index i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.seg_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  const int64_t p = a.seg_p0[lo] + (i - a.seg_off[lo]);
+  if (!unpack) {
+    if (a.hpos) {
+      const float4 x = a.X[p];
+      a.hpos[3 * i] = x.x; a.hpos[3 * i + 1] = x.y; a.hpos[3 * i + 2] = x.z;
+    }
+    if (a.hvel) {
+      const float4 v = a.V[p];
+      a.hvel[3 * i] = v.x; a.hvel[3 * i + 1] = v.y; a.hvel[3 * i + 2] = v.z;
+    }
+  } else {
+    if (a.hpos) {
+      float4 x = a.X[p];
+      x.x = a.hpos[3 * i]; x.y = a.hpos[3 * i + 1]; x.z = a.hpos[3 * i + 2];
+      a.X[p] = x;
+    }
+    if (a.hvel) a.V[p] = make_float4(a.hvel[3 * i], a.hvel[3 * i + 1], a.hvel[3 * i + 2], 0.f);
+  }
+}
+
+inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+int launch_predict(const PredictArgs &a, cudaStream_t s) {
+  if (a.np <= 0) return 0;
+  k_predict<<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+  return 1;
+}
+
+int launch_cells(const CellArgs &a, cudaStream_t s) {
+  if (a.np <= 0) return 0;
+  k_cells<<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+  return 1;
+}
+
+int launch_neighbors(const NbrArgs &a, cudaStream_t s) {
+  if (a.np <= 0) return 0;
+  k_neighbors<<<blocks_for(a.np, 128), 128, 0, s>>>(a);
+  return 1;
+}
+
+int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s) {
+  if (a.nbodies <= 0) return 0;
+  (void)warps_per_block;
+  k_iterate<<<blocks_for(a.nbodies, 4), 128, 0, s>>>(a);
+  return 1;
+}
+
+int launch_wrench(const WrenchArgs &a, cudaStream_t s) {
+  if (a.nb <= 0) return 0;
+  k_wrench<<<blocks_for(a.nb, 4), 128, 0, s>>>(a);
+  return 1;
+}
+
+int launch_pack(const PackArgs &a, int unpack, cudaStream_t s) {
+  if (a.total <= 0) return 0;
+  k_pack<<<blocks_for(a.total, 256), 256, 0, s>>>(a, unpack);
+  return 1;
+}
+
+}  // namespace pbdr

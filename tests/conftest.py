@@ -19,3 +19,19 @@ def orc():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def pbdr_lib():
+    """The sm_103a library (built in place); loading fails loudly if missing."""
+    from paper_2603_14634_gb300 import build as B
+    B.build()
+    from paper_2603_14634_gb300 import binding
+    return binding
+
+
+@pytest.fixture()
+def ctx(pbdr_lib):
+    c = pbdr_lib.Context(0)
+    yield c
+    c.close()

@@ -1,0 +1,355 @@
+"""GPU PBD-R substep vs the FP64 oracle from identical FP32 states.
+
+Tolerances (one substep):
+- positions within 1e-5 m;
+- per-body linear momentum within 1e-6 of the body's momentum scale
+  sum_p m_p |v_p|; angular momentum within 4 K 2^-24 of sum_p m_p |r_p| |v_p|
+  (every one of the K iterations re-rounds r, v and the body sums in FP32,
+  which bounds how well L can be carried: 2.4e-6 at K = 10, 4.8e-6 at
+  K = 20); plus, for bodies that
+  touch the ground or another body, the FP32 resolution of the contact
+  impulses: each of the K iterations computes a contact correction from FP32
+  positions, good to a few units in the last place u(|x|) of the coordinates,
+  i.e. (K/dt) sum_{p in contact} m_p 8 u(|x_p|) in momentum (times the body
+  radius for L).  A resting body's bottom layer sits ~1e-5 m deep with
+  u(0.05 m) = 3.7e-9 m, so its support impulse is only resolved to ~4e-4.
+Trajectories: errors against the closed forms of the analytic tests within
+1.05x the oracle's own error + 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2603_14634_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+MOM_TOL = 1e-6
+G = 9.81
+
+
+def _ulp32(x):
+    x = np.maximum(np.abs(x), 1e-30)
+    return 2.0 ** (np.floor(np.log2(x)) - 23)
+
+
+def _contact_particles(orc, sc, *states):
+    """particles within the contact band (2.2 r of another body, 1.5 r of the
+    ground) in any of the given FP32/FP64 states"""
+    bid = orc.body_index(sc.body_off)
+    n = np.array(sc.plane[:3], np.float64)
+    hit = np.zeros(sc.num_particles, bool)
+    for x in states:
+        off, idx = orc.neighbors(np.asarray(x, np.float32), bid, sc.radius)
+        hit |= np.diff(off) > 0
+        hit |= (np.asarray(x, np.float64) @ n - sc.plane[3]) < 1.5 * sc.radius
+    return hit
+
+
+def _check_momenta(orc, sc, x0, pos, vel, o, label, check_P=True, check_L=True):
+    m = 1.0 / sc.inv_mass.astype(np.float64)
+    hit = _contact_particles(orc, sc, x0, pos, o.x)
+    K, dt = sc.iterations, sc.dt
+    worst = 0.0
+    for b in range(sc.num_bodies):
+        s0, s1 = sc.body_off[b], sc.body_off[b + 1]
+        mb = m[s0:s1, None]
+        vg, vo = vel[s0:s1].astype(np.float64), o.v[s0:s1]
+        cg = (mb * pos[s0:s1]).sum(0) / mb.sum()
+        co = (mb * o.x[s0:s1]).sum(0) / mb.sum()
+        rg, ro = pos[s0:s1] - cg, o.x[s0:s1] - co
+        dP = np.linalg.norm((mb * vg).sum(0) - (mb * vo).sum(0))
+        dL = np.linalg.norm(np.cross(rg, mb * vg).sum(0) - np.cross(ro, mb * vo).sum(0))
+        sP = (mb[:, 0] * np.linalg.norm(vo, axis=1)).sum()
+        sL = (mb[:, 0] * np.linalg.norm(ro, axis=1) * np.linalg.norm(vo, axis=1)).sum()
+        xmag = np.maximum(np.abs(o.x[s0:s1]).max(1), sc.radius)
+        contact = (K / dt) * (mb[:, 0] * 8 * _ulp32(xmag))[hit[s0:s1]].sum()
+        rad = np.linalg.norm(ro, axis=1).max() + sc.radius
+        boundP = MOM_TOL * sP + contact
+        boundL = 4 * K * 2.0 ** -24 * sL + contact * rad
+        if check_P:
+            assert dP <= boundP, f"{label}: body {b} |dP| {dP:.3e} > {boundP:.3e} (contact part {contact:.2e})"
+        if check_L:
+            assert dL <= boundL, f"{label}: body {b} |dL| {dL:.3e} > {boundL:.3e}"
+        if not hit[s0:s1].any():
+            worst = max(worst, dP / max(sP, 1e-30))
+    return worst
+
+
+def _compare_one_substep(ctx, orc, sc, state=None, label="", check_P=True, check_L=True):
+    """Both sides start from the same FP32 state (the scene's or `state`)."""
+    sid = ctx.create_scene(sc)
+    o = orc.OracleScene(sc)
+    if state is not None:
+        pos32, vel32 = (np.ascontiguousarray(a, np.float32) for a in state)
+        ctx.write_state(sid, pos32, vel32)
+        o.set_state(pos32, vel32)
+    x_start = o.x.copy()
+    ctx.step(sid, 1)
+    pos, vel, err = ctx.read_state(sid)
+    o.substep(1)
+    assert err == 0, f"{label}: error bits {err}"
+    dx = np.abs(pos - o.x).max()
+    assert dx <= POS_TOL, f"{label}: max |dx| {dx}"
+    rel = _check_momenta(orc, sc, x_start, pos, vel, o, label, check_P, check_L)
+    return dx, rel
+
+
+def test_cube_free_fall(ctx, orc):
+    _compare_one_substep(ctx, orc, scenes.cube_drop(), label="cube drop")
+
+
+def test_cube_impact_and_rest(ctx, orc):
+    sc = scenes.cube_drop()
+    o = orc.OracleScene(sc)
+    for n in (107, 2, 3, 20, 100):   # impact, bounce, settling, rest
+        o.substep(n)
+        _compare_one_substep(ctx, orc, sc, (o.x, o.v), label=f"cube after {n}")
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_bodies_scene(ctx, orc, seed):
+    sc = scenes.random_bodies_scene(seed=seed)
+    _compare_one_substep(ctx, orc, sc, label=f"64 bodies seed {seed}")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_bodies_colliding(ctx, orc, seed):
+    """States evolved by the oracle until bodies touch each other and the
+    ground, then one substep on both sides."""
+    sc = scenes.random_bodies_scene(seed=seed, num_bodies=16)
+    sc.pos = (sc.pos * np.float32(0.8)).astype(np.float32)   # denser: collisions early
+    o = orc.OracleScene(sc)
+    o.substep(120)
+    _compare_one_substep(ctx, orc, sc, (o.x, o.v), label=f"16 bodies colliding seed {seed}")
+
+
+def test_batched_scenes_one_substep(ctx, orc):
+    rng = np.random.default_rng(11)
+    scs = [scenes.batch_scene(rng) for _ in range(8)]
+    states = []
+    for sc in scs:
+        o = orc.OracleScene(sc)
+        o.substep(60)
+        states.append((o.x.astype(np.float32), o.v.astype(np.float32)))
+    ids = [ctx.create_scene(sc) for sc in scs]
+    for sid, (x, v) in zip(ids, states):
+        ctx.write_state(sid, x, v)
+    ctx.step(ids, 1)
+    for sid, sc, (x, v) in zip(ids, scs, states):
+        o = orc.OracleScene(sc)
+        o.set_state(x, v)
+        o.substep(1)
+        pos, vel, err = ctx.read_state(sid)
+        assert err == 0
+        assert np.abs(pos - o.x).max() <= POS_TOL
+        _check_momenta(orc, sc, x, pos, vel, o, f"batched scene {sid}")
+
+
+def test_wrench_one_substep(ctx, orc):
+    for t in (1, 2, 3):
+        sc = scenes.analytic_box(t)
+        o = orc.OracleScene(sc)
+        o.substep(30)
+        _compare_one_substep(ctx, orc, sc, (o.x, o.v), label=f"analytic box {t}")
+
+
+def test_flags_one_substep(ctx, orc):
+    """Ablation flags: positions agree; a momentum is only compared where its
+    correction is kept and the velocity is the incremental one (without them
+    FP32 drifts, which is the paper's point, Sec. III-B and III-C)."""
+    for flags in (scenes.NO_LINMOM, scenes.NO_ANGMOM, scenes.CONTACT_AVG, scenes.STD_VELOCITY):
+        sc = scenes.random_bodies_scene(seed=4, num_bodies=12)
+        sc.pos = (sc.pos * np.float32(0.8)).astype(np.float32)
+        sc.flags = flags
+        o = orc.OracleScene(sc)
+        o.substep(100)
+        _compare_one_substep(ctx, orc, sc, (o.x, o.v), label=f"flags {flags}",
+                             check_P=not (flags & (scenes.NO_LINMOM | scenes.STD_VELOCITY)),
+                             check_L=not (flags & (scenes.NO_ANGMOM | scenes.STD_VELOCITY)))
+
+
+def test_momentum_correction_removes_fp32_drift(ctx, orc):
+    """Sec. III-C: without Eq. lin_momentum the FP32 shape matching leaks
+    linear momentum; with it a free body keeps P to ~1e-6."""
+    errs = {}
+    for flags in (0, scenes.NO_LINMOM):
+        sc = scenes.cube_drop(n=7, clearance=5.0)
+        sc.gravity = (0.0, 0.0, 0.0)
+        c0 = sc.pos.astype(np.float64).mean(0)
+        w = np.array([1.5, -2.0, 1.0])
+        sc.vel = (np.array([0.7, -0.4, 0.2]) + np.cross(w, sc.pos - c0)).astype(np.float32)
+        sc.flags = flags
+        sid = ctx.create_scene(sc)
+        ctx.step(sid, 50)
+        pos, vel, _ = ctx.read_state(sid)
+        P0 = sc.vel.astype(np.float64).sum(0)
+        P1 = vel.astype(np.float64).sum(0)
+        S = np.linalg.norm(sc.vel.astype(np.float64), axis=1).sum()
+        errs[flags] = np.linalg.norm(P1 - P0) / S
+    assert errs[0] < 1e-6 * 50 ** 0.5, errs
+    assert errs[scenes.NO_LINMOM] > 10 * errs[0], errs
+
+
+def test_rest_height_closed_form_on_gpu(ctx):
+    """Bottom layer of the resting 4^3 cube at r - g dt^2 b^K/(1 - b^K),
+    b = 3/4 (the oracle meets this to 1e-12)."""
+    sc = scenes.cube_drop()
+    sid = ctx.create_scene(sc)
+    ctx.step(sid, 240)
+    pos, vel, err = ctx.read_state(sid)
+    beta, K, dt = 0.75, sc.iterations, sc.dt
+    pen = G * dt * dt * beta ** K / (1 - beta ** K)
+    assert err == 0
+    assert np.abs(pos[:16, 2] - (sc.radius - pen)).max() < 1e-4
+    assert np.abs(vel).max() < 1e-3
+
+
+def test_cube_drop_trajectory(ctx, orc):
+    sc = scenes.cube_drop()
+    sid = ctx.create_scene(sc)
+    o = orc.OracleScene(sc)
+    for chunk in range(8):
+        ctx.step(sid, 30)
+        o.substep(30)
+        pos, vel, _ = ctx.read_state(sid)
+        assert np.abs(pos - o.x).max() < 1e-4, f"after {30 * (chunk + 1)} steps"
+
+
+def _analytic(test, x_or_theta, t):
+    if test == 1:
+        return 0.5 * (17.0 - 0.4 * 4.0 * G) / 4.0 * t * t
+    if test == 2:
+        return 0.5 * 0.01 / 0.1 * t * t
+    th = math.pi / 8
+    return 0.5 * (G * math.sin(th) - 0.4 * G * math.cos(th)) * t * t
+
+
+def _measure(test, sc, x):
+    c = x.mean(0)
+    if test == 2:
+        r0 = sc.pos[0, :2] - sc.pos[:, :2].mean(0)
+        r1 = x[0, :2] - c[:2]
+        return math.atan2(r0[0] * r1[1] - r0[1] * r1[0], r0 @ r1)
+    return c[0] - sc.pos.astype(np.float64).mean(0)[0]
+
+
+@pytest.mark.parametrize("test", [1, 2, 3])
+def test_analytic_tests_within_oracle_error(ctx, orc, test):
+    """Table I tests at t = 2 s with Table II parameters: |GPU - analytic| <=
+    1.05 |oracle - analytic| + 1e-4."""
+    T = 2.0
+    sc = scenes.analytic_box(test)
+    n = int(round(T / sc.dt))
+    sid = ctx.create_scene(sc)
+    ctx.step(sid, n)
+    pos, _, err = ctx.read_state(sid)
+    o = orc.OracleScene(sc).substep(n)
+    exp = _analytic(test, None, T)
+    e_gpu = abs(_measure(test, sc, pos.astype(np.float64)) - exp)
+    e_orc = abs(_measure(test, sc, o.x) - exp)
+    assert err == 0
+    assert e_gpu <= 1.05 * e_orc + 1e-4, (e_gpu, e_orc)
+
+
+def test_rigidity_and_momentum_long_run(ctx, orc):
+    """1000 substeps of 64 bodies: every body stays rigid (pairwise
+    distances of its particles within 1e-4 m of the rest shape)."""
+    sc = scenes.random_bodies_scene(seed=0)
+    sid = ctx.create_scene(sc)
+    ctx.step(sid, 1000)
+    pos, vel, err = ctx.read_state(sid)
+    assert err == 0 and np.isfinite(pos).all()
+    for b in range(0, sc.num_bodies, 7):
+        s0, s1 = sc.body_off[b], sc.body_off[b + 1]
+        d0 = np.linalg.norm(sc.pos[s0:s1, None].astype(np.float64) - sc.pos[None, s0:s1], axis=-1)
+        d1 = np.linalg.norm(pos[s0:s1, None].astype(np.float64) - pos[None, s0:s1], axis=-1)
+        assert np.abs(d1 - d0).max() < 1e-4
+    assert pos[:, 2].min() > 0.0          # nothing fell through the ground
+
+
+def test_determinism_and_batch_invariance(pbdr_lib):
+    """Two runs repeat bit for bit, and a scene stepped alone equals the same
+    scene stepped inside a batch of others."""
+    rng = np.random.default_rng(5)
+    scs = [scenes.batch_scene(rng) for _ in range(12)]
+    outs = []
+    for trial in range(2):
+        with pbdr_lib.Context(0) as c:
+            ids = [c.create_scene(s) for s in scs]
+            c.step(ids, 40)
+            outs.append([c.read_state(i)[:2] for i in ids])
+    for a, b in zip(*outs):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    with pbdr_lib.Context(0) as c:
+        sid = c.create_scene(scs[5])
+        c.step(sid, 40)
+        alone = c.read_state(sid)[:2]
+    assert np.array_equal(alone[0], outs[0][5][0]) and np.array_equal(alone[1], outs[0][5][1])
+
+
+def test_nonfinite_state_is_reported(ctx, pbdr_lib):
+    sc = scenes.cube_drop()
+    sid = ctx.create_scene(sc)
+    vel = sc.vel.copy()
+    vel[3, 0] = np.nan
+    ctx.write_state(sid, sc.pos, vel)
+    ctx.step(sid, 1)
+    _, _, err = ctx.read_state(sid)
+    assert err & pbdr_lib.EBIT_NONFINITE
+
+
+def test_invalid_arguments(ctx, pbdr_lib):
+    E = pbdr_lib.PbdrError
+    base = scenes.cube_drop()
+    bad = base.copy()
+    bad.body_off = np.array([0, 40, 30, 64], np.int32)
+    with pytest.raises(E) as e:
+        ctx.create_scene(bad)
+    assert e.value.code == -1
+    for field, val in (("radius", -1.0), ("dt", 0.0), ("iterations", 0), ("plane", (0, 0, 2.0, 0))):
+        b = base.copy()
+        setattr(b, field, val)
+        with pytest.raises(E):
+            ctx.create_scene(b)
+    b = base.copy()
+    b.pos = b.pos.copy()
+    b.pos[0, 0] = np.inf
+    with pytest.raises(E):
+        ctx.create_scene(b)
+    b = base.copy()
+    b.flags = scenes.SM_FROM_XI
+    with pytest.raises(E) as e:
+        ctx.create_scene(b)
+    assert e.value.code == -8
+    sid = ctx.create_scene(base)
+    with pytest.raises(E):
+        ctx.step([sid, sid], 1)
+    with pytest.raises(E):
+        ctx.step([sid + 100], 1)
+    ctx.destroy_scene(sid)
+    with pytest.raises(E):
+        ctx.read_state(sid)
+
+
+def test_budget_exceeded(pbdr_lib):
+    with pbdr_lib.Context(0, hbm_budget_bytes=1 << 20) as c:
+        sc = scenes.random_bodies_scene(seed=0)
+        with pytest.raises(pbdr_lib.PbdrError) as e:
+            c.create_scene(sc)
+        assert e.value.code == -3
+
+
+def test_empty_and_single_particle_scene(ctx, orc):
+    empty = scenes.Scene(pos=np.zeros((0, 3), np.float32), vel=np.zeros((0, 3), np.float32),
+                         inv_mass=np.zeros(0, np.float32), body_off=np.array([0], np.int32))
+    e = ctx.create_scene(empty)
+    one = scenes.Scene(pos=np.array([[0, 0, 0.5]], np.float32), vel=np.zeros((1, 3), np.float32),
+                       inv_mass=np.ones(1, np.float32), body_off=np.array([0, 1], np.int32))
+    s = ctx.create_scene(one)
+    ctx.step([e, s], 3)
+    pos, vel, err = ctx.read_state(s)
+    o = orc.OracleScene(one).substep(3)
+    assert err == 0 and np.abs(pos - o.x).max() < 1e-6
