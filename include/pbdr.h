@@ -189,6 +189,39 @@ int pbdr_neighbor_total(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int64_t
 int pbdr_set_profiling(pbdr_ctx *ctx, int enable);
 int pbdr_read_profile(pbdr_ctx *ctx, double *stage_ms, int64_t *stage_launches, int32_t nstages);
 
+/* ---- allocation-free neighbour stage ---------------------------------- */
+
+/* The paper has no counterpart to this call.  It is the neighbour stage of
+ * one scene (cell keys, stable sort, bucket ranges, neighbour lists, the same
+ * definitions as pbdr_build_neighbors) for callers that must not allocate
+ * device memory themselves: a host framework that owns all device memory
+ * through its own pool or arena, or a control loop whose latency budget an
+ * allocation could break.  It calls no cudaMalloc or cudaFree: its
+ * intermediates live in one fixed ~3 MB __device__ array of the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ *   pos        [n*3] device, FP32 xyz of the scene's particles (taken as x~)
+ *   body       [n] device, body index of every particle
+ *   n          0..65536 (larger n: PBDR_ERR_INVALID)
+ *   radius     particle radius r > 0 (R_n = 2.2 r)
+ *   sorted_key [n] device out: bucket in [0, T), T = smallest power of two >= 2n
+ *   sorted_id  [n] device out: particle indices sorted by key, ascending within a key
+ *   nbr_cnt    [n] device out: full neighbour count of each particle; a count
+ *              above cap means the list was cut at cap entries
+ *   nbr        [cap*n] device out: ascending neighbour indices, column-major
+ *              (slot j of particle p at nbr[j*n + p])
+ *   cap        1..64
+ *   stream     cudaStream_t (NULL = legacy default stream); asynchronous
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents: calls that
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race and must be ordered by the caller. */
+int pbdr_neighbors_noalloc(const float *pos, const int32_t *body, int32_t n, float radius,
+                           uint32_t *sorted_key, uint32_t *sorted_id, int32_t *nbr_cnt,
+                           int32_t *nbr, int32_t cap, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

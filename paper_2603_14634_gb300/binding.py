@@ -30,6 +30,7 @@ EXPORTS = [
     "pbdr_read_states", "pbdr_write_states", "pbdr_scene_info", "pbdr_last_error",
     "pbdr_build_neighbors", "pbdr_read_neighbors", "pbdr_last_launch_count",
     "pbdr_neighbor_total", "pbdr_set_profiling", "pbdr_read_profile",
+    "pbdr_neighbors_noalloc",
 ]
 NUM_STAGES = 5
 STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate")
@@ -91,6 +92,7 @@ def load(path: Optional[str] = None):
     L.pbdr_neighbor_total.argtypes = [vp, P(i32), i32, P(C.c_int64), vp]
     L.pbdr_set_profiling.argtypes = [vp, C.c_int]
     L.pbdr_read_profile.argtypes = [vp, vp, vp, i32]
+    L.pbdr_neighbors_noalloc.argtypes = [vp, vp, i32, C.c_float, vp, vp, vp, vp, i32, vp]
     for name in EXPORTS:
         if name != "pbdr_last_error":
             getattr(L, name).restype = C.c_int
@@ -266,6 +268,15 @@ def pbdr_read_profile(ctx: int):
     ln = np.zeros(NUM_STAGES, np.int64)
     _check(load().pbdr_read_profile(ctx, _ptr(ms), _ptr(ln), NUM_STAGES))
     return {name: (float(ms[k]), int(ln[k])) for k, name in enumerate(STAGES)}
+
+
+def pbdr_neighbors_noalloc(pos_ptr: int, body_ptr: int, n: int, radius: float,
+                           sorted_key_ptr: int, sorted_id_ptr: int, nbr_cnt_ptr: int,
+                           nbr_ptr: int, cap: int = 32, stream=None) -> None:
+    """Allocation-free neighbour stage of one scene on caller-owned device
+    buffers (raw device pointers; see include/pbdr.h)."""
+    _check(load().pbdr_neighbors_noalloc(pos_ptr, body_ptr, n, float(radius), sorted_key_ptr,
+                                         sorted_id_ptr, nbr_cnt_ptr, nbr_ptr, cap, _stream(stream)))
 
 
 class Context:

@@ -84,6 +84,13 @@ struct Plan {
 
 }  // namespace
 
+namespace pbdr {
+int set_last_error(int code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace pbdr
+
 struct pbdr_ctx {
   int device = 0;
   size_t budget = 0;

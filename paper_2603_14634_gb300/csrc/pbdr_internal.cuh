@@ -145,4 +145,7 @@ int radix_sort_pairs(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb,
                      uint32_t *hist, int64_t n, int bits, int *out_in_b,
                      cudaStream_t s);
 
+// records the calling thread's message for pbdr_last_error(); returns code
+int set_last_error(int code, const char *msg);
+
 }  // namespace pbdr
