@@ -180,19 +180,24 @@ def hbm_peak():
 
 
 def kernel_source_sha():
-    src = os.path.join(ROOT, "paper_2603_14634_gb300", "csrc", "pbdr_kernels.cu")
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """hash of every CUDA source of the library (a changed kernel voids the
+    committed ncu traffic figures)"""
+    h = hashlib.sha256()
+    for src in sorted(glob.glob(os.path.join(ROOT, "paper_2603_14634_gb300", "csrc", "*.cu*"))):
+        with open(src, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_particle_iter():
-    """DRAM bytes per particle-iteration of k_iterate from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def ncu_traffic(kernel):
+    """DRAM bytes per unit (particle-iteration or particle-substep) of a
+    kernel from the committed ncu summary, if it was taken on the current
+    kernel sources."""
     sha = kernel_source_sha()
-    for path in glob.glob(os.path.join(ROOT, "profiles", "*k_iterate*.md")):
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"*{kernel}*.md")):
         txt = open(path).read()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-        m_val = re.search(r"dram_bytes_per_particle_iter:\s*([0-9.]+)", txt)
+        m_val = re.search(r"dram_bytes_per_unit:\s*([0-9.]+)", txt)
         if m_sha and m_val and m_sha.group(1) == sha:
             return float(m_val.group(1))
     return None
@@ -296,6 +301,20 @@ def run_pbdr(args, rank, world, local_rank):
         e2e_s = float(t.item())
     e2e_value = work_per_step * world * e2e_steps / e2e_s
 
+    # ---- the streaming form (one launch per stage and per iteration) ----
+    ctx.set_path(streaming=True)
+    with torch.cuda.stream(stream):
+        ctx.step(ids, 2, sh)
+        torch.cuda.synchronize()
+        a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_stream_steps = max(3, min(20, args.steps))
+        a0.record(stream)
+        ctx.step(ids, n_stream_steps, sh)
+        b0.record(stream)
+        torch.cuda.synchronize()
+        streaming_value = work_per_step * n_stream_steps / (a0.elapsed_time(b0) * 1e-3)
+    ctx.set_path(streaming=False)
+
     # ---- one scene per launch on a sample of the same scenes ----
     sample = ids[:: max(1, len(ids) // max(1, args.per_scene_sample))][: args.per_scene_sample]
     s_work = sum(scs[i].num_particles * scs[i].iterations for i in sample)
@@ -329,20 +348,39 @@ def run_pbdr(args, rank, world, local_rank):
             dist.destroy_process_group()
         return None
 
-    # ---- roofline of the dominant kernel (k_iterate, one launch per iteration) ----
-    it_ms, it_launches = prof["iterate"]
-    avg_launch_s = it_ms * 1e-3 / max(it_launches, 1)
-    bytes_per_pi = 84.0 + 4.0 * kbar
-    bytes_per_launch = bytes_per_pi * n_particles
-    achieved = bytes_per_launch / avg_launch_s / 1e9
+    # ---- roofline of the dominant kernel ----
     peak, peak_src = hbm_peak()
-    tr = ncu_traffic_per_particle_iter()
+    dom = max(prof, key=lambda k: prof[k][0])
+    d_ms, d_launches = prof[dom]
+    if dom == "scene_resident":
+        # k_scene_substep: one launch per size class per substep; compulsory
+        # HBM bytes per particle-substep: read X, V, Q (48 B), write X, V
+        # (32 B), write the neighbour lists (4 + 4 kbar B)
+        kernel = "k_scene_substep"
+        bytes_per_unit = 84.0 + 4.0 * kbar
+        units = n_particles
+        unit_name = "particle-substep"
+        sec_per_step = d_ms * 1e-3 / args.steps
+        achieved = bytes_per_unit * units / sec_per_step / 1e9
+        avg_launch_us = d_ms * 1e3 / max(d_launches, 1)
+    else:
+        # k_iterate: one launch per solver iteration; bytes per
+        # particle-iteration: read X, V, Q (48 B), the list count and entries
+        # (4 + 4 kbar B), write X, V (32 B)
+        kernel = "k_iterate"
+        bytes_per_unit = 84.0 + 4.0 * kbar
+        units = n_particles
+        unit_name = "particle-iteration"
+        avg_launch_s = d_ms * 1e-3 / max(d_launches, 1)
+        achieved = bytes_per_unit * units / avg_launch_s / 1e9
+        avg_launch_us = avg_launch_s * 1e6
+    tr = ncu_traffic(kernel)
     roofline = {
-        "bound": "hbm", "kernel": "k_iterate", "achieved": round(achieved, 1), "peak": peak,
+        "bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak,
         "unit": "GB/s", "frac": round(achieved / peak, 4),
-        "traffic": None if tr is None else round(tr * n_particles),
-        "algorithmic_bytes_per_particle_iter": round(bytes_per_pi, 2), "kbar": round(kbar, 3),
-        "avg_launch_us": round(avg_launch_s * 1e6, 2), "peak_source": peak_src,
+        "traffic": None if tr is None else round(tr * units),
+        "algorithmic_bytes": f"{bytes_per_unit:.2f} per {unit_name}", "kbar": round(kbar, 4),
+        "avg_launch_us": round(avg_launch_us, 2), "peak_source": peak_src,
         "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
     }
 
@@ -358,6 +396,8 @@ def run_pbdr(args, rank, world, local_rank):
             "value": round(per_scene_value, 1), "unit": UNIT, "sample_scenes": len(sample),
             "batched_same_sample": round(batched_sample_value, 1),
             "batched_over_per_scene": round(batched_sample_value / per_scene_value, 2)},
+        "streaming_form": {"value": round(streaming_value, 1), "unit": UNIT,
+                           "what": "same batch, one launch per stage and per solver iteration"},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(n_particles * 24),
                 "d2h_bytes_per_step": int(n_particles * 24 + 4 * len(ids)), "steps": e2e_steps,

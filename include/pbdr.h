@@ -169,6 +169,17 @@ int pbdr_read_neighbors(pbdr_ctx *ctx, pbdr_scene scene, uint32_t *sorted_key,
                         uint32_t *sorted_id, int32_t *off, int32_t *idx,
                         int64_t idx_cap, int64_t *idx_count, void *stream);
 
+/* Execution options (each call drops the cached step plans).
+ * PBDR_OPT_PATH: 0 (default) = scenes of up to 8192 particles run in the
+ *   scene-resident kernel (one CTA keeps a scene in shared memory for the
+ *   whole substep), larger scenes in the streaming kernels; 1 = streaming
+ *   kernels for every scene (one launch per stage and per iteration).
+ * PBDR_OPT_FUSED_THREADS: threads per CTA of the scene-resident kernel,
+ *   0 (default) = per size class, else a multiple of 32 in 32..512. */
+#define PBDR_OPT_PATH 1
+#define PBDR_OPT_FUSED_THREADS 2
+int pbdr_set_option(pbdr_ctx *ctx, int32_t option, int64_t value);
+
 /* Launch statistics of the last pbdr_step call: the number of kernel
  * launches it issued (graph nodes counted individually). */
 int pbdr_last_launch_count(pbdr_ctx *ctx, int64_t *launches);
@@ -182,10 +193,11 @@ int pbdr_neighbor_total(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int64_t
 /* Stage timing.  While enabled, pbdr_step records CUDA events on its stream
  * around each stage of every substep (no CUDA graph is used).  Stages:
  * 0 wrench, 1 integration + cell keys, 2 radix sort, 3 cell ranges +
- * neighbour lists, 4 solver iterations (all K launches).  pbdr_read_profile
- * synchronises, returns the summed milliseconds and launch counts per stage
- * (arrays of `nstages` <= 5 entries) and resets the accumulators. */
-#define PBDR_NUM_STAGES 5
+ * neighbour lists, 4 solver iterations (all K launches) - the streaming
+ * form - and 5 the scene-resident kernels (whole substeps).
+ * pbdr_read_profile synchronises, returns the summed milliseconds and launch
+ * counts per stage (arrays of `nstages` <= 6 entries) and resets them. */
+#define PBDR_NUM_STAGES 6
 int pbdr_set_profiling(pbdr_ctx *ctx, int enable);
 int pbdr_read_profile(pbdr_ctx *ctx, double *stage_ms, int64_t *stage_launches, int32_t nstages);
 

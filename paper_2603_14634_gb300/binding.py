@@ -30,10 +30,12 @@ EXPORTS = [
     "pbdr_read_states", "pbdr_write_states", "pbdr_scene_info", "pbdr_last_error",
     "pbdr_build_neighbors", "pbdr_read_neighbors", "pbdr_last_launch_count",
     "pbdr_neighbor_total", "pbdr_set_profiling", "pbdr_read_profile",
-    "pbdr_neighbors_noalloc",
+    "pbdr_neighbors_noalloc", "pbdr_set_option",
 ]
-NUM_STAGES = 5
-STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate")
+NUM_STAGES = 6
+STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate", "scene_resident")
+OPT_PATH = 1
+OPT_FUSED_THREADS = 2
 
 
 class PbdrError(RuntimeError):
@@ -93,6 +95,7 @@ def load(path: Optional[str] = None):
     L.pbdr_set_profiling.argtypes = [vp, C.c_int]
     L.pbdr_read_profile.argtypes = [vp, vp, vp, i32]
     L.pbdr_neighbors_noalloc.argtypes = [vp, vp, i32, C.c_float, vp, vp, vp, vp, i32, vp]
+    L.pbdr_set_option.argtypes = [vp, i32, C.c_int64]
     for name in EXPORTS:
         if name != "pbdr_last_error":
             getattr(L, name).restype = C.c_int
@@ -229,11 +232,17 @@ def pbdr_build_neighbors(ctx: int, ids: Sequence[int], stream=None) -> None:
     _check(load().pbdr_build_neighbors(ctx, p, len(arr), _stream(stream)))
 
 
-def pbdr_read_neighbors(ctx: int, scene: int, stream=None):
-    """-> (sorted_key [N] u32, sorted_id [N] u32, off [N+1] i32, idx i32)"""
+def pbdr_set_option(ctx: int, option: int, value: int) -> None:
+    _check(load().pbdr_set_option(ctx, option, value))
+
+
+def pbdr_read_neighbors(ctx: int, scene: int, stream=None, lists_only: bool = False):
+    """-> (sorted_key [N] u32, sorted_id [N] u32, off [N+1] i32, idx i32);
+    with lists_only the first two are None (the scene-resident kernel keeps
+    only the lists)."""
     n, _ = pbdr_scene_info(ctx, scene)
-    sk = np.zeros(max(n, 1), np.uint32)
-    si = np.zeros(max(n, 1), np.uint32)
+    sk = None if lists_only else np.zeros(max(n, 1), np.uint32)
+    si = None if lists_only else np.zeros(max(n, 1), np.uint32)
     off = np.zeros(n + 1, np.int32)
     cnt = C.c_int64()
     L = load()
@@ -242,6 +251,8 @@ def pbdr_read_neighbors(ctx: int, scene: int, stream=None):
     idx = np.zeros(max(cnt.value, 1), np.int32)
     _check(L.pbdr_read_neighbors(ctx, scene, None, None, None, _ptr(idx), cnt.value,
                                  C.byref(cnt), _stream(stream)))
+    if lists_only:
+        return None, None, off, idx[:cnt.value]
     return sk[:n], si[:n], off, idx[:cnt.value]
 
 
@@ -330,8 +341,14 @@ class Context:
             ids = [int(ids)]
         pbdr_build_neighbors(self.h, ids, stream)
 
-    def read_neighbors(self, sid: int, stream=None):
-        return pbdr_read_neighbors(self.h, sid, stream)
+    def read_neighbors(self, sid: int, stream=None, lists_only: bool = False):
+        return pbdr_read_neighbors(self.h, sid, stream, lists_only)
+
+    def set_option(self, option: int, value: int):
+        pbdr_set_option(self.h, option, value)
+
+    def set_path(self, streaming: bool):
+        pbdr_set_option(self.h, OPT_PATH, 1 if streaming else 0)
 
     def set_body_wrench(self, sid: int, body: int, F, tau):
         pbdr_set_body_wrench(self.h, sid, body, F, tau)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,7 +81,23 @@ struct Plan {
   std::vector<int64_t> seg_off;    // per plan scene: first plan particle (n+1)
   std::vector<uint32_t> hbase_host;
   int sorted_in_b = 0;             // where the last sort left its result
+  // scene-resident form: size classes of scenes, each one persistent launch
+  bool fused = false;
+  struct FClass {
+    int ncap = 0;
+    bool dx_shared = true;
+    int threads = 256;
+    int grid = 0;
+    int32_t n = 0;
+    std::vector<int32_t> ids;
+    DevBuf list;
+  };
+  std::array<FClass, 4> classes;
+  Plan *rest = nullptr;            // scenes too large for a class (streaming form)
 };
+
+constexpr int kClassCaps[4] = {1024, 2048, 4096, 8192};
+constexpr int kClassThreads[4] = {256, 256, 512, 512};
 
 }  // namespace
 
@@ -99,7 +116,15 @@ struct pbdr_ctx {
   int32_t np_used = 0, nb_used = 0;
   int nbr_cap = 32;
   DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
-  DevBuf bodies, wrench, quat, bcom;
+  DevBuf bodies, wrench, quat, bcom, biter;
+  DevBuf dx_scratch, tickets, chunks, partials;
+  int32_t ccap = 0, nc_used = 0;   // chunk (and partial-slot) capacity / use
+  cudaStream_t cls_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+  int path = 0;                    // 0: scene-resident where a scene fits, 1: streaming only
+  int fused_threads = 0;           // 0: per-class default
+  int num_sms = 0;
+  Plan *last_fused_plan = nullptr;
   DevBuf scenes, scene_err;
   std::vector<SceneHost> sh;
   std::vector<BodyRec> bh;
@@ -166,8 +191,14 @@ int dev_grow(pbdr_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
   return PBDR_OK;
 }
 
-int ensure_capacity(pbdr_ctx *c, int32_t np_need, int32_t nb_need, int32_t ns_need) {
+int ensure_capacity(pbdr_ctx *c, int32_t np_need, int32_t nb_need, int32_t ns_need, int32_t nc_need) {
   int rc;
+  if (nc_need > c->ccap) {
+    int32_t cap = std::max(nc_need, std::max(256, c->ccap * 2));
+    if ((rc = dev_grow(c, c->chunks, (size_t)cap * sizeof(Chunk), (size_t)c->nc_used * sizeof(Chunk)))) return rc;
+    if ((rc = dev_grow(c, c->partials, (size_t)cap * kPartialFloats * sizeof(float), 0))) return rc;
+    c->ccap = cap;
+  }
   if (np_need > c->pcap) {
     int32_t cap = std::max(np_need, std::max(1024, c->pcap * 2));
     size_t keep4 = (size_t)c->np_used * sizeof(float4);
@@ -185,6 +216,10 @@ int ensure_capacity(pbdr_ctx *c, int32_t np_need, int32_t nb_need, int32_t ns_ne
       dev_free(c, c->Xinit);
       if ((rc = dev_alloc(c, c->Xinit, (size_t)cap * sizeof(float4)))) return rc;
     }
+    if (c->dx_scratch.p) {
+      dev_free(c, c->dx_scratch);
+      if ((rc = dev_alloc(c, c->dx_scratch, (size_t)cap * sizeof(float4)))) return rc;
+    }
     c->pcap = cap;
   }
   if (nb_need > c->bcap) {
@@ -193,6 +228,7 @@ int ensure_capacity(pbdr_ctx *c, int32_t np_need, int32_t nb_need, int32_t ns_ne
     if ((rc = dev_grow(c, c->wrench, (size_t)cap * sizeof(BodyWrench), (size_t)c->nb_used * sizeof(BodyWrench)))) return rc;
     if ((rc = dev_grow(c, c->quat, (size_t)cap * sizeof(float4), (size_t)c->nb_used * sizeof(float4)))) return rc;
     if ((rc = dev_grow(c, c->bcom, (size_t)cap * sizeof(float4), (size_t)c->nb_used * sizeof(float4)))) return rc;
+    if ((rc = dev_grow(c, c->biter, (size_t)cap * kBodyScratch * sizeof(float4), 0))) return rc;
     c->bcap = cap;
   }
   if (ns_need > c->scap) {
@@ -214,9 +250,12 @@ int check_scene(pbdr_ctx *c, pbdr_scene s) {
   return PBDR_OK;
 }
 
-int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) {
-  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
+int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out, int streaming_only = 0);
+
+// scene-resident plan: scenes grouped by size class, the rest streamed
+int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) {
   std::vector<int32_t> key(ids, ids + n);
+  key.insert(key.begin(), -2);
   auto it = c->plans.find(key);
   if (it != c->plans.end()) {
     *out = it->second.get();
@@ -230,7 +269,68 @@ int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) {
     seen[ids[i]] = 1;
   }
   auto P = std::make_unique<Plan>();
-  P->ids = key;
+  P->ids.assign(ids, ids + n);
+  P->fused = true;
+  std::vector<int32_t> rest;
+  for (int32_t i = 0; i < n; ++i) {
+    const SceneHost &S = c->sh[ids[i]];
+    int k = 0;
+    while (k < 4 && S.np > kClassCaps[k]) ++k;
+    if (k < 4)
+      P->classes[k].ids.push_back(ids[i]);
+    else
+      rest.push_back(ids[i]);
+  }
+  if (!c->num_sms) CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  int rc;
+  for (int k = 0; k < 4; ++k) {
+    Plan::FClass &F = P->classes[k];
+    F.ncap = kClassCaps[k];
+    F.dx_shared = fused_smem_bytes(F.ncap, true) <= 200 * 1024;
+    F.threads = c->fused_threads ? c->fused_threads : kClassThreads[k];
+    F.n = (int32_t)F.ids.size();
+    if (!F.n) continue;
+    // largest scenes first: the persistent CTAs then finish together
+    std::stable_sort(F.ids.begin(), F.ids.end(),
+                     [&](int32_t a, int32_t b) { return c->sh[a].np > c->sh[b].np; });
+    if ((rc = dev_alloc(c, F.list, F.ids.size() * 4))) return rc;
+    CUDA_TRY(cudaMemcpy(F.list.p, F.ids.data(), F.ids.size() * 4, cudaMemcpyHostToDevice));
+    const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.threads);
+    if (per_sm < 1) return fail(PBDR_ERR_CUDA, "scene-resident kernel does not fit on an SM");
+    F.grid = std::min<int>(F.n, per_sm * c->num_sms);
+    if (!F.dx_shared && !c->dx_scratch.p) {
+      if ((rc = dev_alloc(c, c->dx_scratch, (size_t)c->pcap * sizeof(float4)))) return rc;
+    }
+  }
+  if (!c->tickets.p && (rc = dev_alloc(c, c->tickets, 64))) return rc;
+  Plan *raw = P.get();
+  c->plans[key] = std::move(P);
+  if (!rest.empty()) {
+    if ((rc = build_plan(c, rest.data(), (int32_t)rest.size(), &raw->rest, 1))) return rc;
+  }
+  *out = raw;
+  return PBDR_OK;
+}
+
+int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out, int streaming_only) {
+  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
+  if (!streaming_only && c->path == 0) return build_fused_plan(c, ids, n, out);
+  std::vector<int32_t> key(ids, ids + n);
+  key.insert(key.begin(), -1);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    *out = it->second.get();
+    return PBDR_OK;
+  }
+  std::vector<char> seen(c->sh.size(), 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = check_scene(c, ids[i]);
+    if (rc) return rc;
+    if (seen[ids[i]]) return fail(PBDR_ERR_INVALID, "duplicate scene id " + std::to_string(ids[i]));
+    seen[ids[i]] = 1;
+  }
+  auto P = std::make_unique<Plan>();
+  P->ids.assign(ids, ids + n);
   std::vector<int32_t> pmap, bmap;
   P->hbase_host.assign(std::max<size_t>(c->sh.size(), 1), 0u);
   P->seg_off.push_back(0);
@@ -303,9 +403,11 @@ void invalidate_plans(pbdr_ctx *c) {
     for (DevBuf *b : {&P.pmap, &P.bmap, &P.hbase, &P.keys_a, &P.keys_b, &P.vals_a, &P.vals_b,
                       &P.hist, &P.cstart, &P.cend, &P.spos, &P.wlist})
       dev_free(c, *b);
+    for (auto &F : P.classes) dev_free(c, F.list);
   }
   c->plans.clear();
   c->last_nbr_plan = nullptr;
+  c->last_fused_plan = nullptr;
 }
 
 // event of the profiling pool, recorded on s (returns its pool index)
@@ -406,7 +508,63 @@ PredictArgs predict_args(pbdr_ctx *c, Plan &P, const float4 *X0, const float4 *V
   return a;
 }
 
+int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches);
+
+int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
+  if (!c->ev_fork) {
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    for (int k = 0; k < 4; ++k) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming));
+    }
+  }
+  {
+    StageTimer tm(c, s, 5, launches);
+    CUDA_TRY(cudaMemsetAsync(c->tickets.p, 0, 64, s));
+    // the size classes are independent: one forked stream each
+    CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+    for (int k = 0; k < (int)P.classes.size(); ++k) {
+      Plan::FClass &F = P.classes[k];
+      if (!F.n) continue;
+      CUDA_TRY(cudaStreamWaitEvent(c->cls_stream[k], c->ev_fork, 0));
+      FusedArgs a{};
+      a.X = c->X[0].as<float4>();
+      a.V = c->V[0].as<float4>();
+      a.Q = c->Q.as<float4>();
+      a.pbody = c->pbody.as<int32_t>();
+      a.bodies = c->bodies.as<BodyRec>();
+      a.scenes = c->scenes.as<ScenePar>();
+      a.wrench = c->wrench.as<BodyWrench>();
+      a.quat = c->quat.as<float4>();
+      a.bcom = c->bcom.as<float4>();
+      a.biter = c->biter.as<float4>();
+      a.chunks = c->chunks.as<Chunk>();
+      a.partials = c->partials.as<float>();
+      a.dx_scratch = F.dx_shared ? nullptr : c->dx_scratch.as<float4>();
+      a.nbr_cnt = c->nbr_cnt.as<int32_t>();
+      a.nbr = c->nbr.as<int32_t>();
+      a.nbr_stride = c->pcap;
+      a.nbr_cap = std::min(c->nbr_cap, kFusedNbrCap);
+      a.scene_err = c->scene_err.as<uint32_t>();
+      a.scene_list = F.list.as<int32_t>();
+      a.nscenes = F.n;
+      a.ticket = c->tickets.as<uint32_t>() + k;
+      a.ncap = F.ncap;
+      a.grid = F.grid;
+      launches += launch_scene_substep(a, F.threads, c->cls_stream[k]);
+      CUDA_TRY(cudaEventRecord(c->ev_join[k], c->cls_stream[k]));
+    }
+    for (int k = 0; k < (int)P.classes.size(); ++k)
+      if (P.classes[k].n) CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[k], 0));
+    CUDA_TRY(cudaGetLastError());
+  }
+  c->last_fused_plan = &P;
+  if (P.rest) return substep(c, *P.rest, s, launches);
+  return PBDR_OK;
+}
+
 int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
+  if (P.fused) return fused_substep(c, P, s, launches);
   if (P.np == 0) return PBDR_OK;
   const int K = P.kmax;
   float4 *X0 = c->X[0].as<float4>(), *V0 = c->V[0].as<float4>();
@@ -552,6 +710,11 @@ int pbdr_ctx_destroy(pbdr_ctx *c) {
   cudaDeviceSynchronize();
   invalidate_plans(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (int k = 0; k < 4; ++k) {
+    if (c->cls_stream[k]) cudaStreamDestroy(c->cls_stream[k]);
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+  }
   delete c;
   return PBDR_OK;
 }
@@ -594,7 +757,19 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     return fail(PBDR_ERR_INVALID, "context particle or body count overflow");
   const int32_t sid = (int32_t)c->sh.size();
   const int32_t old_pcap = c->pcap;
-  int rc = ensure_capacity(c, c->np_used + N, c->nb_used + B, sid + 1);
+  // work chunks of the scene-resident kernel: up to kChunk particles of one body
+  std::vector<Chunk> chk;
+  int32_t multi = 0;
+  for (int32_t b = 0; b < B; ++b) {
+    const int32_t n = d->body_off[b + 1] - d->body_off[b];
+    const int32_t nk = (n + kChunk - 1) / kChunk;
+    multi += nk > 1;
+    for (int32_t k = 0; k < nk; ++k)
+      chk.push_back(Chunk{c->nb_used + b, c->np_used + d->body_off[b] + k * kChunk,
+                          std::min(kChunk, n - k * kChunk), k});
+  }
+  std::stable_sort(chk.begin(), chk.end(), [](const Chunk &x, const Chunk &y) { return x.count > y.count; });
+  int rc = ensure_capacity(c, c->np_used + N, c->nb_used + B, sid + 1, c->nc_used + (int32_t)chk.size());
   if (rc) return rc;
   if (c->pcap != old_pcap) invalidate_plans(c);
 
@@ -603,6 +778,7 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   std::vector<int32_t> pb(N);
   std::vector<BodyRec> br(B);
   std::vector<float4> com(B);
+  int32_t slot_next = c->nc_used;
   for (int32_t b = 0; b < B; ++b) {
     const int32_t s0 = d->body_off[b], s1 = d->body_off[b + 1];
     double M = 0, cx = 0, cy = 0, cz = 0;
@@ -632,6 +808,9 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
       pb[p] = c->nb_used + b;
     }
     BodyRec &r = br[b];
+    r.slot0 = slot_next;
+    r.nk = (s1 - s0 + kChunk - 1) / kChunk;
+    slot_next += r.nk;
     r.start = c->np_used + s0;
     r.count = s1 - s0;
     r.scene = sid;
@@ -670,6 +849,10 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   P.iterations = d->iterations;
   P.flags = d->flags;
   P.T = table_size(N);
+  P.c0 = c->nc_used;
+  P.nc = (int32_t)chk.size();
+  P.multi_chunk_bodies = multi;
+  P.pad = 0;
   P.p0 = S.p0;
   P.np = N;
   P.b0 = S.b0;
@@ -687,6 +870,8 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     CUDA_TRY(cudaMemcpy(c->bcom.as<float4>() + S.b0, com.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + S.b0, wr.data(), (size_t)B * sizeof(BodyWrench), cudaMemcpyHostToDevice));
   }
+  if (!chk.empty())
+    CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + c->nc_used, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
   c->bh.insert(c->bh.end(), br.begin(), br.end());
@@ -694,6 +879,7 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   c->sh.push_back(S);
   c->np_used += N;
   c->nb_used += B;
+  c->nc_used += (int32_t)chk.size();
   // plans hold per-scene tables sized by the scene count
   invalidate_plans(c);
   *out = sid;
@@ -726,6 +912,11 @@ int pbdr_set_body_wrench(pbdr_ctx *c, pbdr_scene s, int32_t body, const float F[
   S.wrench_bodies += (on ? 1 : 0) - was;
   CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + gb, &w, sizeof(BodyWrench), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(c->bodies.as<BodyRec>() + gb, &c->bh[gb], sizeof(BodyRec), cudaMemcpyHostToDevice));
+  if (S.wrench_bodies)
+    S.par.flags |= kSceneHasWrench;
+  else
+    S.par.flags &= ~kSceneHasWrench;
+  CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + s, &S.par, sizeof(ScenePar), cudaMemcpyHostToDevice));
   if (was != c->bh[gb].has_wrench) invalidate_plans(c);
   return PBDR_OK;
 }
@@ -794,7 +985,7 @@ int pbdr_build_neighbors(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, void *st
   g_err.clear();
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   Plan *P = nullptr;
-  int rc = build_plan(c, ids, n, &P);
+  int rc = build_plan(c, ids, n, &P, 1);
   if (rc) return rc;
   if (P->np == 0) return PBDR_OK;
   cudaStream_t s = (cudaStream_t)stream;
@@ -815,27 +1006,38 @@ int pbdr_read_neighbors(pbdr_ctx *c, pbdr_scene s, uint32_t *sorted_key, uint32_
   if (rc) return rc;
   if (!idx_count) return fail(PBDR_ERR_INVALID, "NULL idx_count");
   Plan *P = c->last_nbr_plan;
-  if (!P) return fail(PBDR_ERR_INVALID, "no neighbour stage has run since the last scene change");
   int pos_in_plan = -1;
-  for (size_t i = 0; i < P->ids.size(); ++i)
-    if (P->ids[i] == s) pos_in_plan = (int)i;
-  if (pos_in_plan < 0) return fail(PBDR_ERR_INVALID, "scene was not part of the last neighbour stage");
+  if (P)
+    for (size_t i = 0; i < P->ids.size(); ++i)
+      if (P->ids[i] == s) pos_in_plan = (int)i;
+  bool fused = false;
+  if (pos_in_plan < 0 && c->last_fused_plan) {
+    for (auto &F : c->last_fused_plan->classes)
+      for (int32_t id : F.ids) fused |= (id == s);
+    if (fused && (sorted_key || sorted_id))
+      return fail(PBDR_ERR_INVALID, "the scene-resident kernel keeps only the neighbour lists; "
+                                    "sorted keys come from pbdr_build_neighbors");
+  }
+  if (pos_in_plan < 0 && !fused)
+    return fail(PBDR_ERR_INVALID, "scene was not part of the last neighbour stage");
   cudaStream_t st = (cudaStream_t)stream;
   CUDA_TRY(cudaStreamSynchronize(st));
   const SceneHost &S = c->sh[s];
   const int32_t N = S.np;
-  const int64_t so = P->seg_off[pos_in_plan];
-  const uint32_t hb = P->hbase_host[s];
   std::vector<uint32_t> k(N), v(N);
-  if (N > 0) {
+  if (N > 0 && !fused) {
+    const int64_t so = P->seg_off[pos_in_plan];
     const uint32_t *sk = P->sorted_in_b ? P->keys_b.as<uint32_t>() : P->keys_a.as<uint32_t>();
     const uint32_t *sv = P->sorted_in_b ? P->vals_b.as<uint32_t>() : P->vals_a.as<uint32_t>();
     CUDA_TRY(cudaMemcpy(k.data(), sk + so, (size_t)N * 4, cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemcpy(v.data(), sv + so, (size_t)N * 4, cudaMemcpyDeviceToHost));
   }
-  for (int32_t i = 0; i < N; ++i) {
-    if (sorted_key) sorted_key[i] = k[i] - hb;
-    if (sorted_id) sorted_id[i] = v[i] - (uint32_t)S.p0;
+  if (!fused) {
+    const uint32_t hb = P->hbase_host[s];
+    for (int32_t i = 0; i < N; ++i) {
+      if (sorted_key) sorted_key[i] = k[i] - hb;
+      if (sorted_id) sorted_id[i] = v[i] - (uint32_t)S.p0;
+    }
   }
   std::vector<int32_t> cnt(N);
   if (N > 0) CUDA_TRY(cudaMemcpy(cnt.data(), c->nbr_cnt.as<int32_t>() + S.p0, (size_t)N * 4, cudaMemcpyDeviceToHost));
@@ -909,6 +1111,26 @@ int pbdr_read_profile(pbdr_ctx *c, double *stage_ms, int64_t *stage_launches, in
     c->stage_ms[k] = 0.0;
     c->stage_launches[k] = 0;
   }
+  return PBDR_OK;
+}
+
+int pbdr_set_option(pbdr_ctx *c, int32_t option, int64_t value) {
+  g_err.clear();
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  switch (option) {
+    case PBDR_OPT_PATH:
+      if (value != 0 && value != 1) return fail(PBDR_ERR_INVALID, "PBDR_OPT_PATH takes 0 or 1");
+      c->path = (int)value;
+      break;
+    case PBDR_OPT_FUSED_THREADS:
+      if (value != 0 && (value < 32 || value > 512 || value % 32))
+        return fail(PBDR_ERR_INVALID, "PBDR_OPT_FUSED_THREADS takes 0 or a multiple of 32 in 32..512");
+      c->fused_threads = (int)value;
+      break;
+    default:
+      return fail(PBDR_ERR_INVALID, "unknown option " + std::to_string(option));
+  }
+  invalidate_plans(c);
   return PBDR_OK;
 }
 

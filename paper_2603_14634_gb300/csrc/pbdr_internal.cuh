@@ -16,7 +16,11 @@ constexpr uint32_t kNoAngMom = PBDR_NO_ANGMOM;
 constexpr uint32_t kContactAvg = PBDR_CONTACT_AVG;
 constexpr uint32_t kSmFromXi = PBDR_SM_FROM_XI;
 
+// internal scene flag (not part of the ABI): the scene has a body with a wrench
+constexpr uint32_t kSceneHasWrench = 1u << 16;
+
 constexpr uint32_t kEmptyCell = 0xFFFFFFFFu;
+constexpr int kFusedNbrCap = 32;   // neighbour slots per particle in the fused kernel
 constexpr int kMaxBodyParticles = 1 << 20;
 
 // Per-scene constants, read by every kernel (one 80-byte record per scene).
@@ -29,14 +33,32 @@ struct alignas(16) ScenePar {
   uint32_t flags;
   uint32_t T;                   // hash-table size (power of two)
   int32_t p0, np, b0, nb;       // global particle and body ranges
+  int32_t c0, nc;               // the scene's work chunks (scene-resident kernel)
+  int32_t multi_chunk_bodies;   // bodies split over more than one chunk
+  int32_t pad;
 };
 
 // Per-body constants.
 struct alignas(16) BodyRec {
   int32_t start, count, scene, has_wrench;
-  float mass, inv_mass, pad0, pad1;
+  float mass, inv_mass;
+  int32_t slot0, nk;            // first partial-sum slot and number of chunks
   float qsx, qsy, qsz, pad2;    // sum_p m_p q_p (FP32 rest offsets; ~0)
 };
+
+// A chunk: up to kChunk particles of one body, processed by one warp of the
+// scene-resident kernel (lane l owns particles l, l+32, ...).  The chunks of
+// a scene are stored largest first; chunk k of a body covers
+// [start + k*kChunk, ...) and writes partial sums to slot slot0 + k.
+constexpr int kChunk = 128;
+struct alignas(16) Chunk {
+  int32_t body;                 // global body index
+  int32_t first;                // global index of the chunk's first particle
+  int32_t count;
+  int32_t k;                    // index of the chunk within its body
+};
+constexpr int kBodyScratch = 12;    // float4 per body in FusedArgs::biter
+constexpr int kPartialFloats = 20;  // floats per partial-sum slot
 
 // Per-body external wrench, set by the host (force, torque) and the
 // per-substep derived accelerations (aF = F/M, alpha = I^-1 tau about c).
@@ -110,6 +132,30 @@ struct IterArgs {
   int32_t k;               // iteration index
 };
 
+// scene-resident substep (one CTA per scene, persistent over a scene list)
+struct FusedArgs {
+  float4 *X, *V;           // state; X keeps x_init until the end of the substep
+  const float4 *Q;
+  const int32_t *pbody;
+  const BodyRec *bodies;
+  const ScenePar *scenes;
+  BodyWrench *wrench;
+  float4 *quat, *bcom;     // per-body warm start and sum anchor, updated
+  float4 *biter;           // per-body scratch: kBodyScratch float4 per body
+  const Chunk *chunks;     // all chunks (scenes index them through c0, nc)
+  float *partials;         // kPartialFloats per slot
+  float4 *dx_scratch;      // global dX / x_asm scratch, or nullptr (shared memory)
+  int32_t *nbr_cnt, *nbr;
+  int64_t nbr_stride;
+  int32_t nbr_cap;
+  uint32_t *scene_err;
+  const int32_t *scene_list;   // scenes of this size class, largest first
+  int32_t nscenes;
+  uint32_t *ticket;        // work counter, zeroed before the launch
+  int32_t ncap;            // particle capacity of the class
+  int32_t grid;
+};
+
 struct WrenchArgs {
   const float4 *X, *Q;
   const BodyRec *bodies;
@@ -135,6 +181,9 @@ int launch_neighbors(const NbrArgs &a, cudaStream_t s);
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_wrench(const WrenchArgs &a, cudaStream_t s);
 int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
+int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s);
+size_t fused_smem_bytes(int ncap, bool dx_shared);
+int fused_max_blocks_per_sm(int ncap, bool dx_shared, int threads);
 
 // Stable LSD radix sort of (key, value) pairs, keys < 2^bits.  Buffers:
 // ka/va hold the input; kb/vb are scratch of the same size; hist holds

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "pbdr_internal.cuh"
+#include "pbdr_math.cuh"
 
 namespace pbdr {
 namespace {
@@ -165,173 +166,6 @@ __global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
   if (cnt > cap) atomicOr(&a.scene_err[s], (uint32_t)PBDR_EBIT_NBR_OVERFLOW);
 }
 
-// ---------------------------------------------------------------------------
-// 3x3 helpers for the per-body solves (every lane computes the same values)
-// ---------------------------------------------------------------------------
-
-struct Mat3 {
-  float m[9];   // row-major
-};
-
-__device__ __forceinline__ void quat_to_mat(float4 q, float *R) {
-  // q = (x, y, z, w), unit
-  const float x = q.x, y = q.y, z = q.z, w = q.w;
-  R[0] = 1.f - 2.f * (y * y + z * z);
-  R[1] = 2.f * (x * y - z * w);
-  R[2] = 2.f * (x * z + y * w);
-  R[3] = 2.f * (x * y + z * w);
-  R[4] = 1.f - 2.f * (x * x + z * z);
-  R[5] = 2.f * (y * z - x * w);
-  R[6] = 2.f * (x * z - y * w);
-  R[7] = 2.f * (y * z + x * w);
-  R[8] = 1.f - 2.f * (x * x + y * y);
-}
-
-// solve the symmetric system S u = g (S = [s00 s01 s02; . s11 s12; . . s22]);
-// returns false if S is not positive definite (leading minors) or singular
-__device__ __forceinline__ bool solve_spd3(float s00, float s01, float s02, float s11, float s12,
-                                           float s22, float3 g, float3 &u, float rel_tol) {
-  const float c00 = s11 * s22 - s12 * s12;
-  const float c01 = s02 * s12 - s01 * s22;
-  const float c02 = s01 * s12 - s02 * s11;
-  const float det = s00 * c00 + s01 * c01 + s02 * c02;
-  const float tr = (s00 + s11 + s22) * (1.f / 3.f);
-  if (!(s00 > 0.f) || !(s00 * s11 - s01 * s01 > 0.f) || !(det > rel_tol * tr * tr * tr)) {
-    u = make_float3(0.f, 0.f, 0.f);
-    return false;
-  }
-  const float c11 = s00 * s22 - s02 * s02;
-  const float c12 = s01 * s02 - s00 * s12;
-  const float c22 = s00 * s11 - s01 * s01;
-  const float id = 1.f / det;
-  u.x = (c00 * g.x + c01 * g.y + c02 * g.z) * id;
-  u.y = (c01 * g.x + c11 * g.y + c12 * g.z) * id;
-  u.z = (c02 * g.x + c12 * g.y + c22 * g.z) * id;
-  return true;
-}
-
-// unit quaternion (x, y, z, w) of a rotation matrix (Shepperd's method:
-// branch on the largest of the trace and the diagonal)
-__device__ __forceinline__ float4 mat_to_quat(const float *R) {
-  const float tr = R[0] + R[4] + R[8];
-  float4 q;
-  if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
-    const float s = 2.f * sqrtf(fmaxf(1.f + tr, 1e-30f));
-    q = make_float4((R[7] - R[5]) / s, (R[2] - R[6]) / s, (R[3] - R[1]) / s, 0.25f * s);
-  } else if (R[0] >= R[4] && R[0] >= R[8]) {
-    const float s = 2.f * sqrtf(fmaxf(1.f + R[0] - R[4] - R[8], 1e-30f));
-    q = make_float4(0.25f * s, (R[1] + R[3]) / s, (R[2] + R[6]) / s, (R[7] - R[5]) / s);
-  } else if (R[4] >= R[8]) {
-    const float s = 2.f * sqrtf(fmaxf(1.f + R[4] - R[0] - R[8], 1e-30f));
-    q = make_float4((R[1] + R[3]) / s, 0.25f * s, (R[5] + R[7]) / s, (R[2] - R[6]) / s);
-  } else {
-    const float s = 2.f * sqrtf(fmaxf(1.f + R[8] - R[0] - R[4], 1e-30f));
-    q = make_float4((R[2] + R[6]) / s, (R[5] + R[7]) / s, 0.25f * s, (R[3] - R[1]) / s);
-  }
-  const float n = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-  return make_float4(q.x * n, q.y * n, q.z * n, q.w * n);
-}
-
-// Orthogonal polar factor of a nonsingular A by Higham's scaled Newton
-// iteration X <- (g X + (g X)^-T)/2, g = (|X^-1|_F / |X|_F)^(1/2).
-// Returns false if A is (nearly) singular or the factor is a reflection.
-__device__ bool polar_higham(const float *A, float *U) {
-  float X[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) X[k] = A[k];
-  for (int it = 0; it < 24; ++it) {
-    // cofactors C_ij: X^-T = C / det
-    const float c0 = X[4] * X[8] - X[5] * X[7], c1 = X[5] * X[6] - X[3] * X[8],
-                c2 = X[3] * X[7] - X[4] * X[6], c3 = X[2] * X[7] - X[1] * X[8],
-                c4 = X[0] * X[8] - X[2] * X[6], c5 = X[1] * X[6] - X[0] * X[7],
-                c6 = X[1] * X[5] - X[2] * X[4], c7 = X[2] * X[3] - X[0] * X[5],
-                c8 = X[0] * X[4] - X[1] * X[3];
-    const float det = X[0] * c0 + X[1] * c1 + X[2] * c2;
-    float nx = 0.f, nc = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) nx += X[k] * X[k];
-    const float C[9] = {c0, c1, c2, c3, c4, c5, c6, c7, c8};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
-    if (!(fabsf(det) > 1e-30f) || !(nx > 0.f)) return false;
-    const float ninv = sqrtf(nc) / fabsf(det);   // |X^-1|_F
-    const float g = sqrtf(ninv / sqrtf(nx));
-    const float a = 0.5f * g, b = 0.5f / (g * det);
-    float diff = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const float xn = a * X[k] + b * C[k];
-      diff += (xn - X[k]) * (xn - X[k]);
-      X[k] = xn;
-    }
-    if (diff < 1e-12f) break;
-  }
-  const float det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-                    X[2] * (X[3] * X[7] - X[4] * X[6]);
-  if (!(det > 0.5f)) return false;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) U[k] = X[k];
-  return true;
-}
-
-// Rotation maximising tr(R^T A) over SO(3) (the rotation of the least-squares
-// rigid fit of shape matching), by Newton steps on SO(3) from the warm start
-// q: with r_i, a_i the columns of R and A, the objective near R is
-// f(th) ~ f + g.th - th^T H th / 2 with g = sum r_i x a_i and
-// H = (sum r_i.a_i) I3 - sym(sum r_i a_i^T), so th = H^-1 g.  If H is not
-// positive definite at the warm start (the start is far from the optimum),
-// the start is replaced by the polar factor from Higham's iteration; where
-// that fails too (singular or inverted A) damped gradient steps are taken.
-__device__ float4 polar_rotation(const float *A, float4 q) {
-  bool restarted = false;
-  for (int it = 0; it < 8; ++it) {
-    float R[9];
-    quat_to_mat(q, R);
-    float3 g = make_float3(0.f, 0.f, 0.f);
-    float M[9];
-    float t = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float3 r = make_float3(R[i], R[3 + i], R[6 + i]);
-      const float3 av = make_float3(A[i], A[3 + i], A[6 + i]);
-      g = g + cross(r, av);
-      t += dot(r, av);
-    }
-    // sum_i r_i a_i^T = R A^T
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        M[3 * r + c] = R[3 * r + 0] * A[3 * c + 0] + R[3 * r + 1] * A[3 * c + 1] +
-                       R[3 * r + 2] * A[3 * c + 2];
-    float3 th;
-    const bool ok = solve_spd3(t - M[0], -0.5f * (M[1] + M[3]), -0.5f * (M[2] + M[6]), t - M[4],
-                               -0.5f * (M[5] + M[7]), t - M[8], g, th, 1e-6f);
-    if (!ok) {
-      float U[9];
-      if (!restarted && polar_higham(A, U)) {
-        restarted = true;
-        q = mat_to_quat(U);
-        continue;
-      }
-      const float gn = sqrtf(dot(g, g));
-      const float den = fabsf(t) + gn + 1e-30f;
-      th = (1.f / den) * g;
-    }
-    const float thn2 = dot(th, th);
-    // q <- normalize(q + (0, th/2) (x) q)
-    const float4 dq = make_float4(0.5f * (th.x * q.w + th.y * q.z - th.z * q.y),
-                                  0.5f * (th.y * q.w + th.z * q.x - th.x * q.z),
-                                  0.5f * (th.z * q.w + th.x * q.y - th.y * q.x),
-                                  -0.5f * (th.x * q.x + th.y * q.y + th.z * q.z));
-    q = make_float4(q.x + dq.x, q.y + dq.y, q.z + dq.z, q.w + dq.w);
-    const float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    q = make_float4(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
-    if (thn2 < 4e-14f) break;   // |th| < 2e-7 rad: at the FP32 noise floor
-  }
-  return q;
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -465,7 +299,7 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
   }
-  const float4 qrot = polar_rotation(A, a.quat[b]);
+  const float4 qrot = shape_rotation(A, a.quat[b]);
   float R[9];
   quat_to_mat(qrot, R);
 
@@ -520,7 +354,7 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
                 s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
     const float tr = s00 + s11 + s22;
     // I = tr(S) I3 - S
-    solve_spd3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, La - Lb, om, 1e-6f);
+    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, La - Lb, om);
   }
 
   // (3) apply the uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
@@ -578,7 +412,7 @@ __global__ void __launch_bounds__(128) k_wrench(WrenchArgs a) {
   const float tr = s00 + s11 + s22;
   BodyWrench wr = a.wrench[b];
   float3 alpha;
-  solve_spd3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, f3(wr.torque), alpha, 1e-6f);
+  solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, f3(wr.torque), alpha);
   const float3 aF = iM * f3(wr.force);
   const float3 c = anc + d;
   wr.aF = make_float4(aF.x, aF.y, aF.z, 0.f);

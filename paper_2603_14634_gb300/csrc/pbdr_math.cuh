@@ -1,0 +1,187 @@
+// Per-body 3x3 math of the PBD-R solver shared by the streaming and the
+// scene-resident kernels: quaternion <-> matrix, symmetric 3x3 solves and
+// the rotation of the shape-matching fit.  Every lane of a warp calls these
+// with identical inputs and gets identical results.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pbdr {
+namespace {
+
+__device__ __forceinline__ float3 m3add(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 m3scale(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float m3dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 m3cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ void quat_to_mat(float4 q, float *R) {
+  // q = (x, y, z, w), unit
+  const float x = q.x, y = q.y, z = q.z, w = q.w;
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - z * w);
+  R[2] = 2.f * (x * z + y * w);
+  R[3] = 2.f * (x * y + z * w);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - x * w);
+  R[6] = 2.f * (x * z - y * w);
+  R[7] = 2.f * (y * z + x * w);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// solve the symmetric system S u = g (S = [s00 s01 s02; . s11 s12; . . s22]);
+// returns false if S is not positive definite (leading minors) or singular
+__device__ __forceinline__ bool solve_spd3(float s00, float s01, float s02, float s11, float s12,
+                                           float s22, float3 g, float3 &u, float rel_tol) {
+  const float c00 = s11 * s22 - s12 * s12;
+  const float c01 = s02 * s12 - s01 * s22;
+  const float c02 = s01 * s12 - s02 * s11;
+  const float det = s00 * c00 + s01 * c01 + s02 * c02;
+  const float tr = (s00 + s11 + s22) * (1.f / 3.f);
+  if (!(s00 > 0.f) || !(s00 * s11 - s01 * s01 > 0.f) || !(det > rel_tol * tr * tr * tr)) {
+    u = make_float3(0.f, 0.f, 0.f);
+    return false;
+  }
+  const float c11 = s00 * s22 - s02 * s02;
+  const float c12 = s01 * s02 - s00 * s12;
+  const float c22 = s00 * s11 - s01 * s01;
+  const float id = 1.f / det;
+  u.x = (c00 * g.x + c01 * g.y + c02 * g.z) * id;
+  u.y = (c01 * g.x + c11 * g.y + c12 * g.z) * id;
+  u.z = (c02 * g.x + c12 * g.y + c22 * g.z) * id;
+  return true;
+}
+
+// unit quaternion (x, y, z, w) of a rotation matrix (Shepperd's method:
+// branch on the largest of the trace and the diagonal)
+__device__ __forceinline__ float4 mat_to_quat(const float *R) {
+  const float tr = R[0] + R[4] + R[8];
+  float4 q;
+  if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + tr, 1e-30f));
+    q = make_float4((R[7] - R[5]) / s, (R[2] - R[6]) / s, (R[3] - R[1]) / s, 0.25f * s);
+  } else if (R[0] >= R[4] && R[0] >= R[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[0] - R[4] - R[8], 1e-30f));
+    q = make_float4(0.25f * s, (R[1] + R[3]) / s, (R[2] + R[6]) / s, (R[7] - R[5]) / s);
+  } else if (R[4] >= R[8]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[4] - R[0] - R[8], 1e-30f));
+    q = make_float4((R[1] + R[3]) / s, 0.25f * s, (R[5] + R[7]) / s, (R[2] - R[6]) / s);
+  } else {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[8] - R[0] - R[4], 1e-30f));
+    q = make_float4((R[2] + R[6]) / s, (R[5] + R[7]) / s, 0.25f * s, (R[3] - R[1]) / s);
+  }
+  const float n = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  return make_float4(q.x * n, q.y * n, q.z * n, q.w * n);
+}
+
+// Orthogonal polar factor of a nonsingular A by Higham's scaled Newton
+// iteration X <- (g X + (g X)^-T)/2, g = (|X^-1|_F / |X|_F)^(1/2).
+// Returns false if A is (nearly) singular or the factor is a reflection.
+__device__ bool polar_higham(const float *A, float *U) {
+  float X[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) X[k] = A[k];
+  for (int it = 0; it < 24; ++it) {
+    // cofactors C_ij: X^-T = C / det
+    const float c0 = X[4] * X[8] - X[5] * X[7], c1 = X[5] * X[6] - X[3] * X[8],
+                c2 = X[3] * X[7] - X[4] * X[6], c3 = X[2] * X[7] - X[1] * X[8],
+                c4 = X[0] * X[8] - X[2] * X[6], c5 = X[1] * X[6] - X[0] * X[7],
+                c6 = X[1] * X[5] - X[2] * X[4], c7 = X[2] * X[3] - X[0] * X[5],
+                c8 = X[0] * X[4] - X[1] * X[3];
+    const float det = X[0] * c0 + X[1] * c1 + X[2] * c2;
+    float nx = 0.f, nc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nx += X[k] * X[k];
+    const float C[9] = {c0, c1, c2, c3, c4, c5, c6, c7, c8};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
+    if (!(fabsf(det) > 1e-30f) || !(nx > 0.f)) return false;
+    const float ninv = sqrtf(nc) / fabsf(det);   // |X^-1|_F
+    const float g = sqrtf(ninv / sqrtf(nx));
+    const float a = 0.5f * g, b = 0.5f / (g * det);
+    float diff = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float xn = a * X[k] + b * C[k];
+      diff += (xn - X[k]) * (xn - X[k]);
+      X[k] = xn;
+    }
+    if (diff < 1e-12f) break;
+  }
+  const float det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                    X[2] * (X[3] * X[7] - X[4] * X[6]);
+  if (!(det > 0.5f)) return false;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) U[k] = X[k];
+  return true;
+}
+
+// Rotation maximising tr(R^T A) over SO(3) (the rotation of the least-squares
+// rigid fit of shape matching), by Newton steps on SO(3) from the warm start
+// q: with r_i, a_i the columns of R and A, the objective near R is
+// f(th) ~ f + g.th - th^T H th / 2 with g = sum r_i x a_i and
+// H = (sum r_i.a_i) I3 - sym(sum r_i a_i^T), so th = H^-1 g.  If H is not
+// positive definite at the warm start (the start is far from the optimum),
+// the start is replaced by the polar factor from Higham's iteration; where
+// that fails too (singular or inverted A) damped gradient steps are taken.
+__device__ __noinline__ float4 shape_rotation(const float *A, float4 q) {
+  bool restarted = false;
+  for (int it = 0; it < 8; ++it) {
+    float R[9];
+    quat_to_mat(q, R);
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    float M[9];
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float3 r = make_float3(R[i], R[3 + i], R[6 + i]);
+      const float3 av = make_float3(A[i], A[3 + i], A[6 + i]);
+      g = m3add(g, m3cross(r, av));
+      t += m3dot(r, av);
+    }
+    // sum_i r_i a_i^T = R A^T
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        M[3 * r + c] = R[3 * r + 0] * A[3 * c + 0] + R[3 * r + 1] * A[3 * c + 1] +
+                       R[3 * r + 2] * A[3 * c + 2];
+    float3 th;
+    const bool ok = solve_spd3(t - M[0], -0.5f * (M[1] + M[3]), -0.5f * (M[2] + M[6]), t - M[4],
+                               -0.5f * (M[5] + M[7]), t - M[8], g, th, 1e-6f);
+    if (!ok) {
+      float U[9];
+      if (!restarted && polar_higham(A, U)) {
+        restarted = true;
+        q = mat_to_quat(U);
+        continue;
+      }
+      const float gn = sqrtf(m3dot(g, g));
+      const float den = fabsf(t) + gn + 1e-30f;
+      th = m3scale(1.f / den, g);
+    }
+    const float thn2 = m3dot(th, th);
+    // q <- normalize(q + (0, th/2) (x) q)
+    const float4 dq = make_float4(0.5f * (th.x * q.w + th.y * q.z - th.z * q.y),
+                                  0.5f * (th.y * q.w + th.z * q.x - th.x * q.z),
+                                  0.5f * (th.z * q.w + th.x * q.y - th.y * q.x),
+                                  -0.5f * (th.x * q.x + th.y * q.y + th.z * q.z));
+    q = make_float4(q.x + dq.x, q.y + dq.y, q.z + dq.z, q.w + dq.w);
+    const float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    q = make_float4(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
+    if (thn2 < 4e-14f) break;   // |th| < 2e-7 rad: at the FP32 noise floor
+  }
+  return q;
+}
+
+
+// I u = g for the symmetric positive definite inertia-like matrix I; u = 0
+// when I is singular (a one-particle or colinear body has no angular part)
+__device__ __forceinline__ void solve_sym3(float s00, float s01, float s02, float s11, float s12,
+                                           float s22, float3 g, float3 &u) {
+  solve_spd3(s00, s01, s02, s11, s12, s22, g, u, 1e-6f);
+}
+
+}  // namespace
+}  // namespace pbdr

@@ -30,8 +30,12 @@ def pbdr_lib():
     return binding
 
 
-@pytest.fixture()
-def ctx(pbdr_lib):
+@pytest.fixture(params=["resident", "streaming"])
+def ctx(pbdr_lib, request):
+    """A context running the scene-resident kernel (default) or the streaming
+    kernels for every scene."""
     c = pbdr_lib.Context(0)
+    c.set_path(streaming=request.param == "streaming")
+    c.path_name = request.param
     yield c
     c.close()

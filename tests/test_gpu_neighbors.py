@@ -84,15 +84,37 @@ def test_predicted_positions_feed_the_lists(ctx, orc):
     sc.pos = (sc.pos * np.float32(0.5)).astype(np.float32)
     sid = ctx.create_scene(sc)
     ctx.step(sid, 1)
-    sk, si, off, idx = ctx.read_neighbors(sid)
-    # sorted ids are a permutation, keys ascending, lists ascending and cross-body
-    assert sorted(si.tolist()) == list(range(sc.num_particles))
-    assert np.all(np.diff(sk.astype(np.int64)) >= 0)
+    resident = ctx.path_name == "resident"
+    sk, si, off, idx = ctx.read_neighbors(sid, lists_only=resident)
+    if not resident:
+        # sorted ids are a permutation, keys ascending
+        assert sorted(si.tolist()) == list(range(sc.num_particles))
+        assert np.all(np.diff(sk.astype(np.int64)) >= 0)
     body = orc.body_index(sc.body_off)
     for p in range(sc.num_particles):
         lst = idx[off[p]:off[p + 1]]
         assert np.all(np.diff(lst) > 0)
         assert np.all(body[lst] != body[p])
+
+
+def test_resident_lists_equal_oracle_on_exact_prediction(ctx, orc):
+    """With zero velocity and zero gravity x~ = x exactly, so the lists the
+    substep builds (either form) are the oracle's lists of the given
+    positions, bit for bit."""
+    rng = np.random.default_rng(3)
+    scs = [scenes.batch_scene(rng) for _ in range(5)]
+    for sc in scs:
+        sc.pos = (sc.pos * np.float32(0.6)).astype(np.float32)
+        sc.vel[:] = 0
+        sc.gravity = (0.0, 0.0, 0.0)
+        sc.plane = (0.0, 0.0, 1.0, -100.0)
+    ids = [ctx.create_scene(s) for s in scs]
+    ctx.step(ids, 1)
+    for sid, sc in zip(ids, scs):
+        _, _, off, idx = ctx.read_neighbors(sid, lists_only=True)
+        o_off, o_idx = orc.neighbors(sc.pos, orc.body_index(sc.body_off), sc.radius, "brute")
+        np.testing.assert_array_equal(off, o_off)
+        np.testing.assert_array_equal(idx, o_idx)
 
 
 def test_overflow_sets_error_bit(ctx, pbdr_lib):

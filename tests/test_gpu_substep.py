@@ -270,7 +270,8 @@ def test_rigidity_and_momentum_long_run(ctx, orc):
     assert pos[:, 2].min() > 0.0          # nothing fell through the ground
 
 
-def test_determinism_and_batch_invariance(pbdr_lib):
+@pytest.mark.parametrize("streaming", [False, True])
+def test_determinism_and_batch_invariance(pbdr_lib, streaming):
     """Two runs repeat bit for bit, and a scene stepped alone equals the same
     scene stepped inside a batch of others."""
     rng = np.random.default_rng(5)
@@ -278,16 +279,44 @@ def test_determinism_and_batch_invariance(pbdr_lib):
     outs = []
     for trial in range(2):
         with pbdr_lib.Context(0) as c:
+            c.set_path(streaming)
             ids = [c.create_scene(s) for s in scs]
             c.step(ids, 40)
             outs.append([c.read_state(i)[:2] for i in ids])
     for a, b in zip(*outs):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     with pbdr_lib.Context(0) as c:
+        c.set_path(streaming)
         sid = c.create_scene(scs[5])
         c.step(sid, 40)
         alone = c.read_state(sid)[:2]
     assert np.array_equal(alone[0], outs[0][5][0]) and np.array_equal(alone[1], outs[0][5][1])
+
+
+def test_mixed_sizes_every_class_and_streaming_rest(ctx, orc):
+    """One batch holding scenes of every size class of the scene-resident
+    kernel (<= 1024, 2048, 4096, 8192 particles) and one larger scene that
+    the streaming kernels take, one substep from oracle-evolved states."""
+    scs = [scenes.random_bodies_scene(seed=s, num_bodies=nb) for s, nb in
+           ((10, 6), (11, 14), (12, 30), (13, 60), (14, 80))]   # 750 .. 10000 particles
+    states = []
+    for sc in scs:
+        sc.pos = (sc.pos * np.float32(0.85)).astype(np.float32)
+        o = orc.OracleScene(sc)
+        o.substep(90)
+        states.append((o.x.astype(np.float32), o.v.astype(np.float32)))
+    ids = [ctx.create_scene(sc) for sc in scs]
+    for sid, (x, v) in zip(ids, states):
+        ctx.write_state(sid, x, v)
+    ctx.step(ids, 1)
+    for sid, sc, (x, v) in zip(ids, scs, states):
+        o = orc.OracleScene(sc)
+        o.set_state(x, v)
+        o.substep(1)
+        pos, vel, err = ctx.read_state(sid)
+        assert err == 0
+        assert np.abs(pos - o.x).max() <= POS_TOL, f"scene of {sc.num_particles}"
+        _check_momenta(orc, sc, x, pos, vel, o, f"scene of {sc.num_particles}")
 
 
 def test_nonfinite_state_is_reported(ctx, pbdr_lib):
