@@ -86,6 +86,7 @@ struct Plan {
   struct FClass {
     int ncap = 0;
     bool dx_shared = true;
+    bool v_shared = true;
     int threads = 256;
     int grid = 0;
     int32_t n = 0;
@@ -286,7 +287,8 @@ int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) 
   for (int k = 0; k < 4; ++k) {
     Plan::FClass &F = P->classes[k];
     F.ncap = kClassCaps[k];
-    F.dx_shared = fused_smem_bytes(F.ncap, true) <= 200 * 1024;
+    F.dx_shared = fused_smem_bytes(F.ncap, true, false) <= 200 * 1024;
+    F.v_shared = F.dx_shared && fused_smem_bytes(F.ncap, true, true) <= 200 * 1024;
     F.threads = c->fused_threads ? c->fused_threads : kClassThreads[k];
     F.n = (int32_t)F.ids.size();
     if (!F.n) continue;
@@ -295,7 +297,7 @@ int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) 
                      [&](int32_t a, int32_t b) { return c->sh[a].np > c->sh[b].np; });
     if ((rc = dev_alloc(c, F.list, F.ids.size() * 4))) return rc;
     CUDA_TRY(cudaMemcpy(F.list.p, F.ids.data(), F.ids.size() * 4, cudaMemcpyHostToDevice));
-    const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.threads);
+    const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.v_shared, F.threads);
     if (per_sm < 1) return fail(PBDR_ERR_CUDA, "scene-resident kernel does not fit on an SM");
     F.grid = std::min<int>(F.n, per_sm * c->num_sms);
     if (!F.dx_shared && !c->dx_scratch.p) {
@@ -551,6 +553,7 @@ int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
       a.ticket = c->tickets.as<uint32_t>() + k;
       a.ncap = F.ncap;
       a.grid = F.grid;
+      a.v_shared = F.v_shared ? 1 : 0;
       launches += launch_scene_substep(a, F.threads, c->cls_stream[k]);
       CUDA_TRY(cudaEventRecord(c->ev_join[k], c->cls_stream[k]));
     }

@@ -50,6 +50,17 @@ __device__ __forceinline__ float d2rn(float3 p, float3 q) {
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+constexpr int kNearMax = 8;   // near bodies kept per body; more marks every particle interface
+
+// u16 array lengths are padded to a multiple of 8 so the next array stays 16-byte aligned
+__device__ __forceinline__ int ncap_even(int n) { return (n + 7) & ~7; }
+// bucket-table capacity of a class: the smallest power of two >= ncap
+__host__ __device__ __forceinline__ int fused_tcap(int ncap) {
+  int t = 1;
+  while (t < ncap) t <<= 1;
+  return t;
+}
+
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -115,8 +126,7 @@ __device__ void block_scan_excl(uint32_t *a, int m, uint32_t *wsums) {
 
 // body sums of phase A -> rotation of the shape-matching fit (Sec. III-C):
 // red = [sum m e (3), sum m e q^T (9), P_bsm (3), sum m e x v (3)], e = x - a
-__device__ __forceinline__ void body_rotation(const float *red, const BodyRec &br, float4 *bt,
-                                              int lane) {
+__device__ __forceinline__ void body_rotation(const float *red, const BodyRec &br, float4 *bt) {
   const float3 cA = mul(br.inv_mass, make_float3(red[0], red[1], red[2]));
   const float3 Pb = make_float3(red[12], red[13], red[14]);
   const float3 Lb = sub(make_float3(red[15], red[16], red[17]), cross3(cA, Pb));
@@ -128,19 +138,16 @@ __device__ __forceinline__ void body_rotation(const float *red, const BodyRec &b
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) A[3 * rr + cc] = red[3 + 3 * rr + cc] - ca[rr] * qs[cc];
   const float4 qrot = shape_rotation(A, bt[0]);
-  __syncwarp();
-  if (lane == 0) {
-    bt[0] = qrot;
-    bt[1] = make_float4(cA.x, cA.y, cA.z, 0.f);
-    bt[2] = make_float4(Pb.x, Pb.y, Pb.z, 0.f);
-    bt[3] = make_float4(Lb.x, Lb.y, Lb.z, 0.f);
-  }
+  bt[0] = qrot;
+  bt[1] = make_float4(cA.x, cA.y, cA.z, 0.f);
+  bt[2] = make_float4(Pb.x, Pb.y, Pb.z, 0.f);
+  bt[3] = make_float4(Lb.x, Lb.y, Lb.z, 0.f);
 }
 
 // body sums of phase B -> momentum corrections (Eqs. lin_momentum,
 // ang_momentum): red = [sum m e (3), P_asm (3), sum m e x v (3), sum m e e^T (6)]
 __device__ __forceinline__ void body_momentum(const float *red, const BodyRec &br, float4 *bt,
-                                              int aslot, int nslot, const ScenePar &sp, int lane) {
+                                              int aslot, int nslot, const ScenePar &sp) {
   const float M = br.mass, iM = br.inv_mass;
   const float3 cA2 = mul(iM, make_float3(red[0], red[1], red[2]));
   const float3 Pa = make_float3(red[3], red[4], red[5]);
@@ -156,29 +163,27 @@ __device__ __forceinline__ void body_momentum(const float *red, const BodyRec &b
     solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, sub(La, Lb), om);
   }
   const float3 anc = f3(bt[aslot]);
-  __syncwarp();
-  if (lane == 0) {
-    bt[4] = make_float4(cA2.x, cA2.y, cA2.z, 0.f);
-    bt[5] = make_float4(dv.x, dv.y, dv.z, 0.f);
-    bt[8] = make_float4(om.x, om.y, om.z, 0.f);
-    const float3 cn = add(add(anc, cA2), mul(sp.dt, dv));   // CoM after the correction
-    bt[nslot] = make_float4(cn.x, cn.y, cn.z, 0.f);
+  bt[4] = make_float4(cA2.x, cA2.y, cA2.z, 0.f);
+  bt[5] = make_float4(dv.x, dv.y, dv.z, 0.f);
+  bt[8] = make_float4(om.x, om.y, om.z, 0.f);
+  const float3 cn = add(add(anc, cA2), mul(sp.dt, dv));   // CoM after the correction
+  bt[nslot] = make_float4(cn.x, cn.y, cn.z, 0.f);
+}
+
+// totals of one body: its chunks' partial sums added in chunk order
+template <int NV>
+__device__ __forceinline__ void body_totals(const float *partials, const BodyRec &br, float *out) {
+  const float *pt = partials + (size_t)kPartialFloats * br.slot0;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = pt[j];
+  for (int k = 1; k < br.nk; ++k) {
+    pt += kPartialFloats;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) out[j] += pt[j];
   }
 }
 
-// totals of a body split over several chunks: lane j adds value j of the
-// chunks' partial sums in chunk order, then every lane receives all totals
-template <int NV>
-__device__ __forceinline__ void sum_partials(const float *partials, const BodyRec &br, int lane,
-                                             float *out) {
-  float mine = 0.f;
-  if (lane < NV)
-    for (int k = 0; k < br.nk; ++k) mine += partials[(size_t)kPartialFloats * (br.slot0 + k) + lane];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) out[j] = __shfl_sync(kFull, mine, j);
-}
-
-template <bool kDxShared, int kMaxThreads, int kMinBlocks>
+template <bool kDxShared, bool kVShared, int kMaxThreads, int kMinBlocks>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int32_t s_scene;
@@ -186,6 +191,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
   float4 *Xs = reinterpret_cast<float4 *>(smem);
   float4 *DXs = kDxShared ? Xs + a.ncap : nullptr;
   unsigned char *build = reinterpret_cast<unsigned char *>(Xs + a.ncap);
+  // velocities of the scene: in shared memory after the DX area, or global
+  float4 *Vsm = kVShared ? Xs + 2 * a.ncap : nullptr;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
 
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     if (N == 0) continue;
     const float dt = sp.dt, idt = sp.inv_dt;
     float4 *DX = kDxShared ? DXs : a.dx_scratch + p0;
+    float4 *Vl = kVShared ? Vsm : a.V + p0;   // velocities, scene-local index
     const bool std_vel = (sp.flags & kStdVelocity) != 0;
 
     // ---- wrench accelerations (aF = F/M, alpha = I^-1 tau about c) --------
@@ -261,26 +269,31 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       const float3 vt = add(f3(v), mul(dt, acc));
       const float3 xt = add(f3(x), mul(dt, vt));
       Xs[i] = make_float4(xt.x, xt.y, xt.z, x.w);
-      a.V[p] = make_float4(vt.x, vt.y, vt.z, 0.f);
+      Vl[i] = make_float4(vt.x, vt.y, vt.z, 0.f);
     }
 
-    // ---- neighbour lists: counting sort of buckets in shared memory ------
-    uint32_t T = 1;
-    while (T < (uint32_t)N) T <<= 1;
-    uint32_t *start = reinterpret_cast<uint32_t *>(build);
-    uint16_t *sidx = reinterpret_cast<uint16_t *>(start + T + 1);
-    uint16_t *lbody = sidx + N;
-    for (uint32_t k = tid; k <= T; k += nt) start[k] = 0u;
+    // ---- neighbour lists ---------------------------------------------------
+    // Only "interface" particles can be in a pair: p within R_n of q puts p
+    // within R_n of the bounding box of q's body.  So (1) every body gets an
+    // oriented bounding box of its x~ in the frame of its warm-start rotation
+    // and a bounding sphere, (2) bodies whose spheres come within R_n of each
+    // other are listed as near, (3) a particle is an interface particle if it
+    // lies within R_n of the box of a body near its own, and (4) only interface
+    // particles are hashed into the grid and searched.  All tests carry
+    // margins that cover FP32 rounding, so the lists are exactly those of the
+    // O(N^2) definition.
+    uint16_t *lbody = reinterpret_cast<uint16_t *>(build);          // [N]
+    uint16_t *slist = lbody + ncap_even(a.ncap);                     // [N] interface particles
+    uint16_t *sidx = slist + ncap_even(a.ncap);                      // [|S|] sorted by bucket
+    uint32_t *start = reinterpret_cast<uint32_t *>(sidx + ncap_even(a.ncap));   // [T+1]
+    uint8_t *cand = reinterpret_cast<uint8_t *>(start + (fused_tcap(a.ncap) + 1));   // [|S|]
+    __shared__ uint32_t s_nS;
+    if (tid == 0) s_nS = 0;
     for (int bl = warp; bl < B; bl += nwarps) {
-      const BodyRec br = a.bodies[b0 + bl];
-      for (int32_t p = br.start + lane; p < br.start + br.count; p += 32)
-        lbody[p - p0] = (uint16_t)bl;
-    }
-    // broad phase: bounding sphere of every body's x~ (slot 9 of the body
-    // scratch: centre, radius grown to cover FP32 rounding)
-    for (int bl = warp; bl < B; bl += nwarps) {
-      const BodyRec br = a.bodies[b0 + bl];
+      const int32_t b = b0 + bl;
+      const BodyRec br = a.bodies[b];
       const int32_t l0 = br.start - p0, l1 = l0 + br.count;
+      for (int32_t i = l0 + lane; i < l1; i += 32) lbody[i] = (uint16_t)bl;
       const float3 o = f3(Xs[l0]);
       float sx = 0.f, sy = 0.f, sz = 0.f;
       for (int32_t i = l0 + lane; i < l1; i += 32) {
@@ -290,44 +303,110 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       sx = wsum(sx); sy = wsum(sy); sz = wsum(sz);
       const float inv = 1.f / (float)br.count;
       const float3 cen = add(o, make_float3(sx * inv, sy * inv, sz * inv));
-      float r2 = 0.f;
+      float R[9];
+      quat_mat(a.quat[b], R);
+      float ex = 0.f, ey = 0.f, ez = 0.f;
       for (int32_t i = l0 + lane; i < l1; i += 32) {
-        const float3 e = sub(f3(Xs[i]), cen);
-        r2 = fmaxf(r2, dot3(e, e));
+        const float3 d = sub(f3(Xs[i]), cen);
+        ex = fmaxf(ex, fabsf(R[0] * d.x + R[3] * d.y + R[6] * d.z));
+        ey = fmaxf(ey, fabsf(R[1] * d.x + R[4] * d.y + R[7] * d.z));
+        ez = fmaxf(ez, fabsf(R[2] * d.x + R[5] * d.y + R[8] * d.z));
       }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, off));
+      for (int off = 16; off > 0; off >>= 1) {
+        ex = fmaxf(ex, __shfl_xor_sync(kFull, ex, off));
+        ey = fmaxf(ey, __shfl_xor_sync(kFull, ey, off));
+        ez = fmaxf(ez, __shfl_xor_sync(kFull, ez, off));
+      }
       if (lane == 0) {
-        const float rad = sqrtf(r2) * (1.f + 1e-5f) + 1e-6f;
-        a.biter[(size_t)kBodyScratch * (b0 + bl) + 9] = make_float4(cen.x, cen.y, cen.z, rad);
+        // grow the box for the rounding of the frame change and of |R| != 1
+        const float g = 1e-5f * (ex + ey + ez + fabsf(cen.x) + fabsf(cen.y) + fabsf(cen.z)) + 1e-6f;
+        ex += g; ey += g; ez += g;
+        const float rad = sqrtf(ex * ex + ey * ey + ez * ez) * (1.f + 1e-5f) + 1e-6f;
+        float4 *bt = a.biter + (size_t)kBodyScratch * b;
+        bt[9] = make_float4(cen.x, cen.y, cen.z, rad);
+        bt[10] = make_float4(ex, ey, ez, 0.f);
       }
     }
     __syncthreads();
-    // a body needs the particle search only if another body's sphere comes
-    // within the neighbour radius of its own (conservative margins)
     const float reach = sqrtf(sp.Rn2) * (1.f + 1e-5f) + 1e-6f;
+    // near bodies (up to kNearMax per body; more marks the body "all")
     for (int bl = tid; bl < B; bl += nt) {
-      const float4 sa = a.biter[(size_t)kBodyScratch * (b0 + bl) + 9];
+      float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
+      const float4 sa = bt[9];
       const float ma = fabsf(sa.x) + fabsf(sa.y) + fabsf(sa.z);
-      int near = 0;
-      for (int bo = 0; bo < B && !near; ++bo) {
+      int nn = 0;
+      uint16_t near[kNearMax];
+      for (int bo = 0; bo < B; ++bo) {
         if (bo == bl) continue;
         const float4 sb = a.biter[(size_t)kBodyScratch * (b0 + bo) + 9];
         const float3 d = make_float3(sa.x - sb.x, sa.y - sb.y, sa.z - sb.z);
         const float lim = sa.w + sb.w + reach +
                           1e-5f * (ma + fabsf(sb.x) + fabsf(sb.y) + fabsf(sb.z) + sa.w + sb.w) + 1e-6f;
-        near = dot3(d, d) <= lim * lim;
+        if (dot3(d, d) <= lim * lim) {
+          if (nn < kNearMax) near[nn] = (uint16_t)bo;
+          ++nn;
+        }
       }
-      a.biter[(size_t)kBodyScratch * (b0 + bl) + 10] = make_float4(near ? 1.f : 0.f, 0.f, 0.f, 0.f);
+      uint32_t packed[kNearMax / 2];
+#pragma unroll
+      for (int k = 0; k < kNearMax / 2; ++k)
+        packed[k] = (2 * k < nn ? near[2 * k] : 0u) | ((2 * k + 1 < nn ? (uint32_t)near[2 * k + 1] : 0u) << 16);
+      bt[11] = make_float4(__uint_as_float(packed[0]), __uint_as_float(packed[1]),
+                           __uint_as_float(packed[2]), __uint_as_float(packed[3]));
+      float4 e = bt[10];
+      e.w = __int_as_float(nn);
+      bt[10] = e;
     }
+    __syncthreads();
+    // interface particles -> compact list
     for (int32_t i = tid; i < N; i += nt) {
-      const float4 x = Xs[i];
+      const int32_t bl = lbody[i];
+      const float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
+      const int nn = __float_as_int(bt[10].w);
+      bool iface = nn > kNearMax;
+      if (nn > 0 && !iface) {
+        const float3 xp = f3(Xs[i]);
+        const float4 pk = bt[11];
+        const uint32_t packed[4] = {__float_as_uint(pk.x), __float_as_uint(pk.y), __float_as_uint(pk.z),
+                                    __float_as_uint(pk.w)};
+        for (int k = 0; k < nn && !iface; ++k) {
+          const int32_t bo = (packed[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+          const int32_t gb = b0 + bo;
+          const float4 *bo_t = a.biter + (size_t)kBodyScratch * gb;
+          const float4 sc = bo_t[9], ext = bo_t[10];
+          float R[9];
+          quat_mat(a.quat[gb], R);
+          const float3 d = sub(xp, f3(sc));
+          const float ux = fmaxf(fabsf(R[0] * d.x + R[3] * d.y + R[6] * d.z) - ext.x, 0.f);
+          const float uy = fmaxf(fabsf(R[1] * d.x + R[4] * d.y + R[7] * d.z) - ext.y, 0.f);
+          const float uz = fmaxf(fabsf(R[2] * d.x + R[5] * d.y + R[8] * d.z) - ext.z, 0.f);
+          const float lim = reach + 1e-5f * (fabsf(d.x) + fabsf(d.y) + fabsf(d.z)) + 1e-6f;
+          iface = ux * ux + uy * uy + uz * uz <= lim * lim;
+        }
+      }
+      if (iface) {
+        const uint32_t at = atomicAdd(&s_nS, 1u);
+        slist[at] = (uint16_t)i;
+      } else {
+        a.nbr_cnt[p0 + i] = 0;
+      }
+    }
+    __syncthreads();
+    const int32_t nS = (int32_t)s_nS;
+    uint32_t T = 1;
+    while (T < (uint32_t)nS) T <<= 1;
+    for (uint32_t k = tid; k <= T; k += nt) start[k] = 0u;
+    __syncthreads();
+    for (int32_t s = tid; s < nS; s += nt) {
+      const float4 x = Xs[slist[s]];
       const uint32_t key = chash(cellc(x.x, sp.inv_h), cellc(x.y, sp.inv_h), cellc(x.z, sp.inv_h)) & (T - 1u);
       atomicAdd(&start[key], 1u);
     }
     __syncthreads();
     block_scan_excl(start, (int)T + 1, s_wsums);
-    for (int32_t i = tid; i < N; i += nt) {
+    for (int32_t s = tid; s < nS; s += nt) {
+      const int32_t i = slist[s];
       const float4 x = Xs[i];
       const uint32_t key = chash(cellc(x.x, sp.inv_h), cellc(x.y, sp.inv_h), cellc(x.z, sp.inv_h)) & (T - 1u);
       const uint32_t at = atomicAdd(&start[key], 1u);
@@ -336,13 +415,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     __syncthreads();
     // start[k] now holds the end of bucket k; bucket k = [start[k-1], start[k])
     const int cap = a.nbr_cap;
-    for (int32_t i = tid; i < N; i += nt) {
+    for (int32_t s = tid; s < nS; s += nt) {
+      const int32_t i = slist[s];
       const float3 xp = f3(Xs[i]);
       const uint16_t bp = lbody[i];
-      if (a.biter[(size_t)kBodyScratch * (b0 + bp) + 10].x == 0.f) {   // no other body in reach
-        a.nbr_cnt[p0 + i] = 0;
-        continue;
-      }
       const int32_t ix = cellc(xp.x, sp.inv_h), iy = cellc(xp.y, sp.inv_h), iz = cellc(xp.z, sp.inv_h);
       int32_t list[kFusedNbrCap];
       int cnt = 0;
@@ -374,7 +450,13 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       for (int k = 0; k < nw; ++k) a.nbr[(int64_t)k * a.nbr_stride + p0 + i] = p0 + list[k];
       a.nbr_cnt[p0 + i] = nw;
       if (cnt > cap) atomicOr(&a.scene_err[sid], (uint32_t)PBDR_EBIT_NBR_OVERFLOW);
+      cand[s] = nw > 0;
     }
+    __syncthreads();
+    // a negative w in shared memory marks a particle with contact candidates
+    // (the list is only read for those)
+    for (int32_t s = tid; s < nS; s += nt)
+      if (cand[s]) Xs[slist[s]].w = -Xs[slist[s]].w;
     __syncthreads();
 
     // ---- K solver iterations over chunks ------------------------------------
@@ -384,7 +466,6 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     // while its chunks still use the current one.
     const Chunk *ch = a.chunks + sp.c0;
     const int NC = sp.nc;
-    const bool multi = sp.multi_chunk_bodies > 0;
     for (int bl = tid; bl < B; bl += nt) {
       float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
       bt[0] = a.quat[b0 + bl];
@@ -395,48 +476,61 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     const float3 nrm = make_float3(sp.nx, sp.ny, sp.nz);
     for (int it = 0; it < sp.iterations; ++it) {
       const int aslot = 6 + (it & 1), nslot = 6 + ((it + 1) & 1);
-      // (A) contacts from X_i (Jacobi) and the first body sums, per chunk
+      // (A) contacts from X_i (Jacobi) and the first body sums, per chunk;
+      // each lane owns up to kChunk/32 = 4 particles of the chunk
       for (int c = warp; c < NC; c += nwarps) {
         const Chunk C = ch[c];
         const BodyRec br = a.bodies[C.body];
-        float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
+        const float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
         const float3 anc = f3(bt[aslot]);
+        const int32_t l0 = C.first - p0, l1 = l0 + C.count;
+        float4 q4[kChunk / 32];
+#pragma unroll
+        for (int j = 0; j < kChunk / 32; ++j) {
+          const int32_t i = l0 + lane + 32 * j;
+          if (i < l1) q4[j] = __ldg(a.Q + p0 + i);
+        }
         float red[18];
 #pragma unroll
         for (int k = 0; k < 18; ++k) red[k] = 0.f;
-        const int32_t l0 = C.first - p0, l1 = l0 + C.count;
-        for (int32_t i = l0 + lane; i < l1; i += 32) {
+#pragma unroll
+        for (int j = 0; j < kChunk / 32; ++j) {
+          const int32_t i = l0 + lane + 32 * j;
+          if (i >= l1) continue;
           const int32_t p = p0 + i;
           const float4 xp = Xs[i];
-          const float4 vp = a.V[p];
+          const float4 vp = Vl[i];
           float3 dX = make_float3(0.f, 0.f, 0.f);
           const float pen_g = r - (dot3(nrm, f3(xp)) - sp.nd);
           if (pen_g > 0.f) dX = sub(mul(pen_g, nrm), friction(mul(dt, f3(vp)), nrm, mu * pen_g));
-          const int32_t cnt = a.nbr_cnt[p];
-          float3 acc = make_float3(0.f, 0.f, 0.f);
-          int active = 0;
-          for (int32_t j = 0; j < cnt; ++j) {
-            const int32_t q = a.nbr[(int64_t)j * a.nbr_stride + p];
-            const float4 xq = Xs[q - p0];
-            const float3 diff = sub(f3(xp), f3(xq));
-            const float dd = dot3(diff, diff);
-            if (dd > 0.f && dd < dc * dc) {
-              const float d = sqrtf(dd);
-              const float pen = dc - d;
-              const float3 nh = mul(1.f / d, diff);
-              const float4 vq = a.V[q];
-              const float sw = xp.w / (xp.w + xq.w);
-              const float3 del = mul(dt, sub(f3(vp), f3(vq)));
-              acc = add(acc, mul(sw, sub(mul(pen, nh), friction(del, nh, mu * pen))));
-              ++active;
+          if (xp.w < 0.f) {   // particle with contact candidates
+            const int32_t cnt = a.nbr_cnt[p];
+            float3 acc = make_float3(0.f, 0.f, 0.f);
+            int active = 0;
+            for (int32_t jj = 0; jj < cnt; ++jj) {
+              const int32_t q = a.nbr[(int64_t)jj * a.nbr_stride + p];
+              const float4 xq = Xs[q - p0];
+              const float3 diff = sub(f3(xp), f3(xq));
+              const float dd = dot3(diff, diff);
+              if (dd > 0.f && dd < dc * dc) {
+                const float d = sqrtf(dd);
+                const float pen = dc - d;
+                const float3 nh = mul(1.f / d, diff);
+                const float4 vq = Vl[q - p0];
+                const float wp = fabsf(xp.w), wq = fabsf(xq.w);
+                const float sw = wp / (wp + wq);
+                const float3 del = mul(dt, sub(f3(vp), f3(vq)));
+                acc = add(acc, mul(sw, sub(mul(pen, nh), friction(del, nh, mu * pen))));
+                ++active;
+              }
             }
+            if ((sp.flags & kContactAvg) && active > 0) acc = mul(1.f / (float)active, acc);
+            dX = add(dX, acc);
           }
-          if ((sp.flags & kContactAvg) && active > 0) acc = mul(1.f / (float)active, acc);
-          dX = add(dX, acc);
           DX[i] = make_float4(dX.x, dX.y, dX.z, 0.f);
           const float3 xb = add(f3(xp), dX);
           const float3 vb = std_vel ? mul(idt, sub(xb, f3(a.X[p]))) : add(f3(vp), mul(idt, dX));
-          const float4 q = a.Q[p];
+          const float4 q = q4[j];
           const float m = q.w;
           const float3 e = sub(xb, anc);
           const float3 me = mul(m, e);
@@ -450,44 +544,50 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         }
 #pragma unroll
         for (int k = 0; k < 18; ++k) red[k] = wsum(red[k]);
-        if (br.nk == 1) {
-          body_rotation(red, br, bt, lane);
-        } else if (lane == 0) {
+        if (lane == 0) {
           float *pt = a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
 #pragma unroll
           for (int k = 0; k < 18; ++k) pt[k] = red[k];
         }
       }
       __syncthreads();
-      if (multi) {   // bodies split over several chunks: sum the chunk partials in chunk order
-        for (int bl = warp; bl < B; bl += nwarps) {
-          const BodyRec br = a.bodies[b0 + bl];
-          if (br.nk <= 1) continue;
-          float red[18];
-          sum_partials<18>(a.partials, br, lane, red);
-          body_rotation(red, br, a.biter + (size_t)kBodyScratch * (b0 + bl), lane);
-        }
-        __syncthreads();
+      // (A2) one thread per body: totals over the body's chunks (chunk order)
+      // and the rotation of the shape-matching fit
+      for (int bl = tid; bl < B; bl += nt) {
+        const BodyRec br = a.bodies[b0 + bl];
+        float red[18];
+        body_totals<18>(a.partials, br, red);
+        body_rotation(red, br, a.biter + (size_t)kBodyScratch * (b0 + bl));
       }
+      __syncthreads();
       // (B) shape-matching goals g = R q + c -> X_asm, V_asm and the second sums
       for (int c = warp; c < NC; c += nwarps) {
         const Chunk C = ch[c];
         const BodyRec br = a.bodies[C.body];
-        float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
+        const float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
         const float3 anc = f3(bt[aslot]);
         float R[9];
         quat_mat(bt[0], R);
         const float3 cA = f3(bt[1]);
+        const int32_t l0 = C.first - p0, l1 = l0 + C.count;
+        float4 q4[kChunk / 32];
+#pragma unroll
+        for (int j = 0; j < kChunk / 32; ++j) {
+          const int32_t i = l0 + lane + 32 * j;
+          if (i < l1) q4[j] = __ldg(a.Q + p0 + i);
+        }
         float red[15];
 #pragma unroll
         for (int k = 0; k < 15; ++k) red[k] = 0.f;
-        const int32_t l0 = C.first - p0, l1 = l0 + C.count;
-        for (int32_t i = l0 + lane; i < l1; i += 32) {
+#pragma unroll
+        for (int j = 0; j < kChunk / 32; ++j) {
+          const int32_t i = l0 + lane + 32 * j;
+          if (i >= l1) continue;
           const int32_t p = p0 + i;
           const float4 xi = Xs[i];
           const float3 dX = f3(DX[i]);
-          const float4 vi = a.V[p];
-          const float4 q = a.Q[p];
+          const float4 vi = Vl[i];
+          const float4 q = q4[j];
           const float m = q.w;
           const float3 xb = add(f3(xi), dX);
           const float3 vb = std_vel ? mul(idt, sub(xb, f3(a.X[p]))) : add(f3(vi), mul(idt, dX));
@@ -498,7 +598,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           const float3 xa = add(xb, dsm);
           const float3 va = std_vel ? mul(idt, sub(xa, f3(a.X[p]))) : add(vb, mul(idt, dsm));
           DX[i] = make_float4(xa.x, xa.y, xa.z, 0.f);
-          a.V[p] = make_float4(va.x, va.y, va.z, 0.f);
+          Vl[i] = make_float4(va.x, va.y, va.z, 0.f);
           const float3 e = sub(xa, anc);
           const float3 me = mul(m, e);
           red[0] += me.x; red[1] += me.y; red[2] += me.z;
@@ -510,25 +610,21 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         }
 #pragma unroll
         for (int k = 0; k < 15; ++k) red[k] = wsum(red[k]);
-        if (br.nk == 1) {
-          body_momentum(red, br, bt, aslot, nslot, sp, lane);
-        } else if (lane == 0) {
+        if (lane == 0) {
           float *pt = a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
 #pragma unroll
           for (int k = 0; k < 15; ++k) pt[k] = red[k];
         }
       }
       __syncthreads();
-      if (multi) {
-        for (int bl = warp; bl < B; bl += nwarps) {
-          const BodyRec br = a.bodies[b0 + bl];
-          if (br.nk <= 1) continue;
-          float red[15];
-          sum_partials<15>(a.partials, br, lane, red);
-          body_momentum(red, br, a.biter + (size_t)kBodyScratch * (b0 + bl), aslot, nslot, sp, lane);
-        }
-        __syncthreads();
+      // (B2) one thread per body: momentum corrections
+      for (int bl = tid; bl < B; bl += nt) {
+        const BodyRec br = a.bodies[b0 + bl];
+        float red[15];
+        body_totals<15>(a.partials, br, red);
+        body_momentum(red, br, a.biter + (size_t)kBodyScratch * (b0 + bl), aslot, nslot, sp);
       }
+      __syncthreads();
       // (C) uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
       for (int c = warp; c < NC; c += nwarps) {
         const Chunk C = ch[c];
@@ -538,15 +634,14 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         bool bad = false;
         const int32_t l0 = C.first - p0, l1 = l0 + C.count;
         for (int32_t i = l0 + lane; i < l1; i += 32) {
-          const int32_t p = p0 + i;
           const float3 xa = f3(DX[i]);
-          const float3 va = f3(a.V[p]);
+          const float3 va = f3(Vl[i]);
           const float3 rr = sub(sub(xa, anc), cA2);
           const float3 corr = sub(dv, cross3(om, rr));
           const float3 v = add(va, corr);
           const float3 x = add(xa, mul(dt, corr));
           Xs[i] = make_float4(x.x, x.y, x.z, Xs[i].w);
-          a.V[p] = make_float4(v.x, v.y, v.z, 0.f);
+          Vl[i] = make_float4(v.x, v.y, v.z, 0.f);
           bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
         }
         if (__any_sync(kFull, bad) && lane == 0) atomicOr(&a.scene_err[sid], (uint32_t)PBDR_EBIT_NONFINITE);
@@ -559,32 +654,45 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       a.bcom[b0 + bl] = bt[6 + (sp.iterations & 1)];
     }
     // ---- write the substep's positions back ------------------------------
-    for (int32_t i = tid; i < N; i += nt) a.X[p0 + i] = Xs[i];
+    for (int32_t i = tid; i < N; i += nt) {
+      const float4 x = Xs[i];
+      a.X[p0 + i] = make_float4(x.x, x.y, x.z, fabsf(x.w));
+      if (kVShared) a.V[p0 + i] = Vl[i];
+    }
     __syncthreads();
   }
 }
 
 }  // namespace
 
-size_t fused_smem_bytes(int ncap, bool dx_shared) {
-  // X (16 B) + max(DX 16 B, build area) per particle
-  size_t build = 4 * ((size_t)2 * ncap + 1) + 4 * (size_t)ncap;   // start[T'+1] + sidx + lbody
+size_t fused_smem_bytes(int ncap, bool dx_shared, bool v_shared) {
+  // X (16 B per particle) + max(DX 16 B per particle, neighbour build area:
+  // lbody, interface list, sorted list (u16 each), bucket starts u32[T+1]
+  // with T <= the smallest power of two >= ncap)
+  size_t pad = ((size_t)ncap + 7) & ~(size_t)7;
+  const size_t tcap = (size_t)fused_tcap(ncap);
+  size_t build = 3 * 2 * pad + 4 * (tcap + 1) + pad;   // + candidate flags
   size_t dxa = dx_shared ? 16 * (size_t)ncap : 0;
-  return 16 * (size_t)ncap + (dxa > build ? dxa : build);
+  return 16 * (size_t)ncap + (dxa > build ? dxa : build) + (v_shared ? 16 * (size_t)ncap : 0);
 }
 
 // kernel variant for a launch: <= 256 threads with registers capped for
 // three CTAs per SM, else <= 512 threads for one CTA per SM
-template <bool kDx>
+template <bool kDx, bool kV>
 static void *variant(int threads) {
-  return threads <= 256 ? (void *)k_scene_substep<kDx, 256, 3> : (void *)k_scene_substep<kDx, 512, 1>;
+  return threads <= 256 ? (void *)k_scene_substep<kDx, kV, 256, 3> : (void *)k_scene_substep<kDx, kV, 512, 1>;
+}
+
+static void *pick(bool dx, bool v, int threads) {
+  if (dx) return v ? variant<true, true>(threads) : variant<true, false>(threads);
+  return v ? variant<false, true>(threads) : variant<false, false>(threads);
 }
 
 int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s) {
   if (a.nscenes <= 0) return 0;
   const bool dxs = a.dx_scratch == nullptr;
-  const size_t smem = fused_smem_bytes(a.ncap, dxs);
-  void *fn = dxs ? variant<true>(threads) : variant<false>(threads);
+  const size_t smem = fused_smem_bytes(a.ncap, dxs, a.v_shared != 0);
+  void *fn = pick(dxs, a.v_shared != 0, threads);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   FusedArgs arg = a;
   void *params[] = {&arg};
@@ -592,9 +700,9 @@ int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s) {
   return 1;
 }
 
-int fused_max_blocks_per_sm(int ncap, bool dx_shared, int threads) {
-  const size_t smem = fused_smem_bytes(ncap, dx_shared);
-  void *fn = dx_shared ? variant<true>(threads) : variant<false>(threads);
+int fused_max_blocks_per_sm(int ncap, bool dx_shared, bool v_shared, int threads) {
+  const size_t smem = fused_smem_bytes(ncap, dx_shared, v_shared);
+  void *fn = pick(dx_shared, v_shared, threads);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);

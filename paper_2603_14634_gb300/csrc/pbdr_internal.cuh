@@ -154,6 +154,7 @@ struct FusedArgs {
   uint32_t *ticket;        // work counter, zeroed before the launch
   int32_t ncap;            // particle capacity of the class
   int32_t grid;
+  int32_t v_shared;        // velocities held in shared memory during the substep
 };
 
 struct WrenchArgs {
@@ -182,8 +183,8 @@ int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_wrench(const WrenchArgs &a, cudaStream_t s);
 int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
 int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s);
-size_t fused_smem_bytes(int ncap, bool dx_shared);
-int fused_max_blocks_per_sm(int ncap, bool dx_shared, int threads);
+size_t fused_smem_bytes(int ncap, bool dx_shared, bool v_shared);
+int fused_max_blocks_per_sm(int ncap, bool dx_shared, bool v_shared, int threads);
 
 // Stable LSD radix sort of (key, value) pairs, keys < 2^bits.  Buffers:
 // ka/va hold the input; kb/vb are scratch of the same size; hist holds

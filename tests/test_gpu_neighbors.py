@@ -129,3 +129,34 @@ def test_overflow_sets_error_bit(ctx, pbdr_lib):
     assert err & pbdr_lib.EBIT_NBR_OVERFLOW
     _, _, err = ctx.read_state(sid)      # bits clear on read
     assert err == 0
+
+
+
+def test_lists_exact_with_rotated_bodies(ctx, orc):
+    """The scene-resident kernel bounds bodies by boxes in the frame of their
+    last shape-matching rotation.  Spin the bodies first so those frames are
+    not the rest frame, then zero the velocities (x~ = x exactly) and compare
+    the lists of the next substep with the O(N^2) definition."""
+    rng = np.random.default_rng(21)
+    scs = [scenes.batch_scene(rng) for _ in range(4)]
+    ids = []
+    for sc in scs:
+        sc.pos = (sc.pos * np.float32(0.7)).astype(np.float32)
+        sc.gravity = (0.0, 0.0, 0.0)
+        sc.plane = (0.0, 0.0, 1.0, -100.0)
+        ids.append(ctx.create_scene(sc))
+    ctx.step(ids, 40)
+    written = {}
+    for sid in ids:
+        pos, _, _ = ctx.read_state(sid)
+        ctx.write_state(sid, pos, np.zeros_like(pos))
+        written[sid] = pos
+    ctx.step(ids, 1)
+    total = 0
+    for sid, sc in zip(ids, scs):
+        _, _, off, idx = ctx.read_neighbors(sid, lists_only=True)
+        o_off, o_idx = orc.neighbors(written[sid], orc.body_index(sc.body_off), sc.radius, "brute")
+        np.testing.assert_array_equal(off, o_off)
+        np.testing.assert_array_equal(idx, o_idx)
+        total += idx.size
+    assert total > 0
