@@ -30,12 +30,14 @@ EXPORTS = [
     "pbdr_read_states", "pbdr_write_states", "pbdr_scene_info", "pbdr_last_error",
     "pbdr_build_neighbors", "pbdr_read_neighbors", "pbdr_last_launch_count",
     "pbdr_neighbor_total", "pbdr_set_profiling", "pbdr_read_profile",
-    "pbdr_neighbors_noalloc", "pbdr_set_option",
+    "pbdr_neighbors_noalloc", "pbdr_set_option", "pbdr_plan_config",
 ]
 NUM_STAGES = 6
 STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate", "scene_resident")
 OPT_PATH = 1
 OPT_FUSED_THREADS = 2
+OPT_GRAPHS = 3
+OPT_AUTOTUNE = 4
 
 
 class PbdrError(RuntimeError):
@@ -96,6 +98,7 @@ def load(path: Optional[str] = None):
     L.pbdr_read_profile.argtypes = [vp, vp, vp, i32]
     L.pbdr_neighbors_noalloc.argtypes = [vp, vp, i32, C.c_float, vp, vp, vp, vp, i32, vp]
     L.pbdr_set_option.argtypes = [vp, i32, C.c_int64]
+    L.pbdr_plan_config.argtypes = [vp, P(i32), i32, vp, i32]
     for name in EXPORTS:
         if name != "pbdr_last_error":
             getattr(L, name).restype = C.c_int
@@ -236,6 +239,15 @@ def pbdr_set_option(ctx: int, option: int, value: int) -> None:
     _check(load().pbdr_set_option(ctx, option, value))
 
 
+def pbdr_plan_config(ctx: int, ids: Sequence[int]):
+    """-> list of per-class dicts (capacity, scenes, threads, v_shared, ctas)"""
+    arr, p = _ids(ids)
+    out = np.zeros(20, np.int32)
+    _check(load().pbdr_plan_config(ctx, p, len(arr), _ptr(out), 20))
+    keys = ("capacity", "scenes", "threads", "v_shared", "ctas")
+    return [dict(zip(keys, map(int, out[5 * k:5 * k + 5]))) for k in range(4)]
+
+
 def pbdr_read_neighbors(ctx: int, scene: int, stream=None, lists_only: bool = False):
     """-> (sorted_key [N] u32, sorted_id [N] u32, off [N+1] i32, idx i32);
     with lists_only the first two are None (the scene-resident kernel keeps
@@ -346,6 +358,9 @@ class Context:
 
     def set_option(self, option: int, value: int):
         pbdr_set_option(self.h, option, value)
+
+    def plan_config(self, ids):
+        return pbdr_plan_config(self.h, ids)
 
     def set_path(self, streaming: bool):
         pbdr_set_option(self.h, OPT_PATH, 1 if streaming else 0)

@@ -95,6 +95,9 @@ struct Plan {
   };
   std::array<FClass, 4> classes;
   Plan *rest = nullptr;            // scenes too large for a class (streaming form)
+  bool tuned = false;              // launch shapes picked by the autotuner
+  cudaGraphExec_t graph = nullptr; // one substep, captured
+  int64_t graph_launches = 0;
 };
 
 constexpr int kClassCaps[4] = {1024, 2048, 4096, 8192};
@@ -117,12 +120,14 @@ struct pbdr_ctx {
   int32_t np_used = 0, nb_used = 0;
   int nbr_cap = 32;
   DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
-  DevBuf bodies, wrench, quat, bcom, biter;
+  DevBuf bodies, wrench, quat, bcom, biter, border;
   DevBuf dx_scratch, tickets, chunks, partials;
   int32_t ccap = 0, nc_used = 0;   // chunk (and partial-slot) capacity / use
   cudaStream_t cls_stream[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
   int path = 0;                    // 0: scene-resident where a scene fits, 1: streaming only
+  bool use_graphs = true;          // replay a captured CUDA graph per substep
+  bool autotune = true;            // time launch shapes on the first step of a plan
   int fused_threads = 0;           // 0: per-class default
   int num_sms = 0;
   Plan *last_fused_plan = nullptr;
@@ -230,6 +235,7 @@ int ensure_capacity(pbdr_ctx *c, int32_t np_need, int32_t nb_need, int32_t ns_ne
     if ((rc = dev_grow(c, c->quat, (size_t)cap * sizeof(float4), (size_t)c->nb_used * sizeof(float4)))) return rc;
     if ((rc = dev_grow(c, c->bcom, (size_t)cap * sizeof(float4), (size_t)c->nb_used * sizeof(float4)))) return rc;
     if ((rc = dev_grow(c, c->biter, (size_t)cap * kBodyScratch * sizeof(float4), 0))) return rc;
+    if ((rc = dev_grow(c, c->border, (size_t)cap * sizeof(int32_t), (size_t)c->nb_used * sizeof(int32_t)))) return rc;
     c->bcap = cap;
   }
   if (ns_need > c->scap) {
@@ -287,8 +293,8 @@ int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) 
   for (int k = 0; k < 4; ++k) {
     Plan::FClass &F = P->classes[k];
     F.ncap = kClassCaps[k];
-    F.dx_shared = fused_smem_bytes(F.ncap, true, false) <= 200 * 1024;
-    F.v_shared = F.dx_shared && fused_smem_bytes(F.ncap, true, true) <= 200 * 1024;
+    F.dx_shared = fused_layout(F.ncap, true, false, true).bytes <= 220 * 1024;
+    F.v_shared = F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024;
     F.threads = c->fused_threads ? c->fused_threads : kClassThreads[k];
     F.n = (int32_t)F.ids.size();
     if (!F.n) continue;
@@ -406,6 +412,8 @@ void invalidate_plans(pbdr_ctx *c) {
                       &P.hist, &P.cstart, &P.cend, &P.spos, &P.wlist})
       dev_free(c, *b);
     for (auto &F : P.classes) dev_free(c, F.list);
+    if (P.graph) cudaGraphExecDestroy(P.graph);
+    P.graph = nullptr;
   }
   c->plans.clear();
   c->last_nbr_plan = nullptr;
@@ -512,49 +520,68 @@ PredictArgs predict_args(pbdr_ctx *c, Plan &P, const float4 *X0, const float4 *V
 
 int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches);
 
-int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
-  if (!c->ev_fork) {
-    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-    for (int k = 0; k < 4; ++k) {
-      CUDA_TRY(cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking));
-      CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming));
-    }
+// one persistent launch of size class k of a scene-resident plan on stream st
+int launch_class(pbdr_ctx *c, Plan &P, int k, cudaStream_t st) {
+  Plan::FClass &F = P.classes[k];
+  FusedArgs a{};
+  a.X = c->X[0].as<float4>();
+  a.V = c->V[0].as<float4>();
+  a.Q = c->Q.as<float4>();
+  a.pbody = c->pbody.as<int32_t>();
+  a.bodies = c->bodies.as<BodyRec>();
+  a.scenes = c->scenes.as<ScenePar>();
+  a.wrench = c->wrench.as<BodyWrench>();
+  a.quat = c->quat.as<float4>();
+  a.bcom = c->bcom.as<float4>();
+  a.biter = c->biter.as<float4>();
+  a.chunks = c->chunks.as<Chunk>();
+  a.border = c->border.as<int32_t>();
+  a.partials = c->partials.as<float>();
+  a.dx_scratch = F.dx_shared ? nullptr : c->dx_scratch.as<float4>();
+  a.nbr_cnt = c->nbr_cnt.as<int32_t>();
+  a.nbr = c->nbr.as<int32_t>();
+  a.nbr_stride = c->pcap;
+  a.nbr_cap = std::min(c->nbr_cap, kFusedNbrCap);
+  a.scene_err = c->scene_err.as<uint32_t>();
+  a.scene_list = F.list.as<int32_t>();
+  a.nscenes = F.n;
+  a.ticket = c->tickets.as<uint32_t>() + k;
+  a.ncap = F.ncap;
+  a.grid = F.grid;
+  a.v_shared = F.v_shared ? 1 : 0;
+  const FusedLayout L = fused_layout(F.ncap, F.dx_shared, F.v_shared, F.dx_shared);
+  a.tcap = L.tcap;
+  a.ccap = L.ccap;
+  a.v_off = L.v_off;
+  a.part_off = L.part_off;
+  a.smem_bytes = L.bytes;
+  return launch_scene_substep(a, F.threads, st);
+}
+
+int ensure_class_streams(pbdr_ctx *c) {
+  if (c->ev_fork) return PBDR_OK;
+  CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  for (int k = 0; k < 4; ++k) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming));
   }
+  return PBDR_OK;
+}
+
+int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches);
+
+int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
+  int rc = ensure_class_streams(c);
+  if (rc) return rc;
   {
     StageTimer tm(c, s, 5, launches);
     CUDA_TRY(cudaMemsetAsync(c->tickets.p, 0, 64, s));
     // the size classes are independent: one forked stream each
     CUDA_TRY(cudaEventRecord(c->ev_fork, s));
     for (int k = 0; k < (int)P.classes.size(); ++k) {
-      Plan::FClass &F = P.classes[k];
-      if (!F.n) continue;
+      if (!P.classes[k].n) continue;
       CUDA_TRY(cudaStreamWaitEvent(c->cls_stream[k], c->ev_fork, 0));
-      FusedArgs a{};
-      a.X = c->X[0].as<float4>();
-      a.V = c->V[0].as<float4>();
-      a.Q = c->Q.as<float4>();
-      a.pbody = c->pbody.as<int32_t>();
-      a.bodies = c->bodies.as<BodyRec>();
-      a.scenes = c->scenes.as<ScenePar>();
-      a.wrench = c->wrench.as<BodyWrench>();
-      a.quat = c->quat.as<float4>();
-      a.bcom = c->bcom.as<float4>();
-      a.biter = c->biter.as<float4>();
-      a.chunks = c->chunks.as<Chunk>();
-      a.partials = c->partials.as<float>();
-      a.dx_scratch = F.dx_shared ? nullptr : c->dx_scratch.as<float4>();
-      a.nbr_cnt = c->nbr_cnt.as<int32_t>();
-      a.nbr = c->nbr.as<int32_t>();
-      a.nbr_stride = c->pcap;
-      a.nbr_cap = std::min(c->nbr_cap, kFusedNbrCap);
-      a.scene_err = c->scene_err.as<uint32_t>();
-      a.scene_list = F.list.as<int32_t>();
-      a.nscenes = F.n;
-      a.ticket = c->tickets.as<uint32_t>() + k;
-      a.ncap = F.ncap;
-      a.grid = F.grid;
-      a.v_shared = F.v_shared ? 1 : 0;
-      launches += launch_scene_substep(a, F.threads, c->cls_stream[k]);
+      launches += launch_class(c, P, k, c->cls_stream[k]);
       CUDA_TRY(cudaEventRecord(c->ev_join[k], c->cls_stream[k]));
     }
     for (int k = 0; k < (int)P.classes.size(); ++k)
@@ -563,6 +590,108 @@ int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   }
   c->last_fused_plan = &P;
   if (P.rest) return substep(c, *P.rest, s, launches);
+  return PBDR_OK;
+}
+
+// Autotuner of the scene-resident kernel: for every size class, times the
+// candidate launch shapes (threads per CTA, velocities in shared memory or
+// not, CTAs per SM) on class-only substeps and keeps the fastest.  The
+// kernel's results do not depend on its launch shape, and the state the
+// trial substeps change is saved before and restored after, so tuning has
+// no effect on the simulation.
+int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
+  int rc;
+  const size_t nX = (size_t)std::max(c->np_used, 1) * sizeof(float4);
+  const size_t nB = (size_t)std::max(c->nb_used, 1) * sizeof(float4);
+  const size_t nE = (size_t)std::max<size_t>(c->sh.size(), 1) * sizeof(uint32_t);
+  DevBuf sX, sV, sQr, sCm, sE;
+  if ((rc = dev_alloc(c, sX, nX)) || (rc = dev_alloc(c, sV, nX)) || (rc = dev_alloc(c, sQr, nB)) ||
+      (rc = dev_alloc(c, sCm, nB)) || (rc = dev_alloc(c, sE, nE)))
+    return rc;
+  CUDA_TRY(cudaMemcpyAsync(sX.p, c->X[0].p, nX, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(sV.p, c->V[0].p, nX, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(sQr.p, c->quat.p, nB, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(sCm.p, c->bcom.p, nB, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(sE.p, c->scene_err.p, nE, cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  for (int k = 0; k < (int)P.classes.size(); ++k) {
+    Plan::FClass &F = P.classes[k];
+    if (!F.n) continue;
+    const int threads_c[3] = {128, 256, 512};
+    float best = 1e30f;
+    int bt = F.threads, bg = F.grid;
+    bool bv = F.v_shared;
+    for (int ti = 0; ti < 3; ++ti) {
+      for (int vs = 0; vs < 2; ++vs) {
+        const bool vsh = vs == 1;
+        if (vsh && !(F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024)) continue;
+        const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, vsh, threads_c[ti]);
+        if (per_sm < 1) continue;
+        const int cps_c[2] = {per_sm, std::max(1, per_sm / 2)};
+        for (int ci = 0; ci < (per_sm > 1 ? 2 : 1); ++ci) {
+          F.threads = threads_c[ti];
+          F.v_shared = vsh;
+          F.grid = std::min<int>(F.n, cps_c[ci] * c->num_sms);
+          for (int rep = 0; rep < 3; ++rep) {
+            if (rep == 1) CUDA_TRY(cudaEventRecord(e0, s));
+            CUDA_TRY(cudaMemsetAsync(c->tickets.as<uint32_t>() + k, 0, 4, s));
+            launch_class(c, P, k, s);
+          }
+          CUDA_TRY(cudaEventRecord(e1, s));
+          CUDA_TRY(cudaEventSynchronize(e1));
+          CUDA_TRY(cudaGetLastError());
+          float ms = 0.f;
+          CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            bt = F.threads;
+            bv = F.v_shared;
+            bg = F.grid;
+          }
+        }
+      }
+    }
+    F.threads = bt;
+    F.v_shared = bv;
+    F.grid = bg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CUDA_TRY(cudaMemcpyAsync(c->X[0].p, sX.p, nX, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->V[0].p, sV.p, nX, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->quat.p, sQr.p, nB, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->bcom.p, sCm.p, nB, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->scene_err.p, sE.p, nE, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (DevBuf *b : {&sX, &sV, &sQr, &sCm, &sE}) dev_free(c, *b);
+  P.tuned = true;
+  return PBDR_OK;
+}
+
+// captures one substep of the plan into a CUDA graph (not on the legacy
+// default stream, which cannot be captured)
+int capture_plan(pbdr_ctx *c, Plan &P, cudaStream_t s) {
+  int rc = ensure_class_streams(c);
+  if (rc) return rc;
+  int64_t launches = 0;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  rc = substep(c, P, s, launches);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(PBDR_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&P.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    P.graph = nullptr;
+    return fail(PBDR_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  P.graph_launches = launches;
   return PBDR_OK;
 }
 
@@ -875,6 +1004,14 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   }
   if (!chk.empty())
     CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + c->nc_used, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+  if (B > 0) {   // the scene's bodies, largest first (owner-warp order of the scene-resident kernel)
+    std::vector<int32_t> ord(B);
+    for (int32_t b = 0; b < B; ++b) ord[b] = c->nb_used + b;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+      return br[x - c->nb_used].count > br[y - c->nb_used].count;
+    });
+    CUDA_TRY(cudaMemcpy(c->border.as<int32_t>() + c->nb_used, ord.data(), (size_t)B * 4, cudaMemcpyHostToDevice));
+  }
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
   c->bh.insert(c->bh.end(), br.begin(), br.end());
@@ -933,9 +1070,25 @@ int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, v
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   int64_t launches = 0;
-  for (int32_t k = 0; k < substeps; ++k) {
-    rc = substep(c, *P, s, launches);
+  if (substeps > 0 && P->fused && c->autotune && !P->tuned) {
+    rc = autotune_fused(c, *P, s);
     if (rc) return rc;
+  }
+  const bool graphs = c->use_graphs && !c->profiling && s != nullptr && substeps > 0;
+  if (graphs && !P->graph) {
+    rc = capture_plan(c, *P, s);
+    if (rc) return rc;
+  }
+  for (int32_t k = 0; k < substeps; ++k) {
+    if (graphs) {
+      CUDA_TRY(cudaGraphLaunch(P->graph, s));
+      launches += P->graph_launches;
+      if (P->fused) c->last_fused_plan = P;
+      if (!P->fused || P->rest) c->last_nbr_plan = P->fused ? P->rest : P;
+    } else {
+      rc = substep(c, *P, s, launches);
+      if (rc) return rc;
+    }
   }
   c->last_launches = launches;
   return PBDR_OK;
@@ -1125,6 +1278,12 @@ int pbdr_set_option(pbdr_ctx *c, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return fail(PBDR_ERR_INVALID, "PBDR_OPT_PATH takes 0 or 1");
       c->path = (int)value;
       break;
+    case PBDR_OPT_GRAPHS:
+      c->use_graphs = value != 0;
+      break;
+    case PBDR_OPT_AUTOTUNE:
+      c->autotune = value != 0;
+      break;
     case PBDR_OPT_FUSED_THREADS:
       if (value != 0 && (value < 32 || value > 512 || value % 32))
         return fail(PBDR_ERR_INVALID, "PBDR_OPT_FUSED_THREADS takes 0 or a multiple of 32 in 32..512");
@@ -1134,6 +1293,23 @@ int pbdr_set_option(pbdr_ctx *c, int32_t option, int64_t value) {
       return fail(PBDR_ERR_INVALID, "unknown option " + std::to_string(option));
   }
   invalidate_plans(c);
+  return PBDR_OK;
+}
+
+int pbdr_plan_config(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t *out, int32_t cap) {
+  g_err.clear();
+  if (!c || !out || cap < 20) return fail(PBDR_ERR_INVALID, "need an output array of 20 int32");
+  Plan *P = nullptr;
+  int rc = build_plan(c, ids, n, &P);
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k) {
+    const bool has = P->fused;
+    out[5 * k + 0] = has ? P->classes[k].ncap : 0;
+    out[5 * k + 1] = has ? P->classes[k].n : 0;
+    out[5 * k + 2] = has ? P->classes[k].threads : 0;
+    out[5 * k + 3] = has ? (P->classes[k].v_shared ? 1 : 0) : 0;
+    out[5 * k + 4] = has ? P->classes[k].grid : 0;
+  }
   return PBDR_OK;
 }
 

@@ -124,65 +124,6 @@ __device__ void block_scan_excl(uint32_t *a, int m, uint32_t *wsums) {
   __syncthreads();
 }
 
-// body sums of phase A -> rotation of the shape-matching fit (Sec. III-C):
-// red = [sum m e (3), sum m e q^T (9), P_bsm (3), sum m e x v (3)], e = x - a
-__device__ __forceinline__ void body_rotation(const float *red, const BodyRec &br, float4 *bt) {
-  const float3 cA = mul(br.inv_mass, make_float3(red[0], red[1], red[2]));
-  const float3 Pb = make_float3(red[12], red[13], red[14]);
-  const float3 Lb = sub(make_float3(red[15], red[16], red[17]), cross3(cA, Pb));
-  float A[9];
-  const float qs[3] = {br.qsx, br.qsy, br.qsz};
-  const float ca[3] = {cA.x, cA.y, cA.z};
-#pragma unroll
-  for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) A[3 * rr + cc] = red[3 + 3 * rr + cc] - ca[rr] * qs[cc];
-  const float4 qrot = shape_rotation(A, bt[0]);
-  bt[0] = qrot;
-  bt[1] = make_float4(cA.x, cA.y, cA.z, 0.f);
-  bt[2] = make_float4(Pb.x, Pb.y, Pb.z, 0.f);
-  bt[3] = make_float4(Lb.x, Lb.y, Lb.z, 0.f);
-}
-
-// body sums of phase B -> momentum corrections (Eqs. lin_momentum,
-// ang_momentum): red = [sum m e (3), P_asm (3), sum m e x v (3), sum m e e^T (6)]
-__device__ __forceinline__ void body_momentum(const float *red, const BodyRec &br, float4 *bt,
-                                              int aslot, int nslot, const ScenePar &sp) {
-  const float M = br.mass, iM = br.inv_mass;
-  const float3 cA2 = mul(iM, make_float3(red[0], red[1], red[2]));
-  const float3 Pa = make_float3(red[3], red[4], red[5]);
-  const float3 La = sub(make_float3(red[6], red[7], red[8]), cross3(cA2, Pa));
-  const float3 Pb = f3(bt[2]), Lb = f3(bt[3]);
-  float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
-  if (!(sp.flags & kNoLinMom)) dv = mul(iM, sub(Pb, Pa));
-  if (!(sp.flags & kNoAngMom)) {
-    const float s00 = red[9] - M * cA2.x * cA2.x, s01 = red[10] - M * cA2.x * cA2.y,
-                s02 = red[11] - M * cA2.x * cA2.z, s11 = red[12] - M * cA2.y * cA2.y,
-                s12 = red[13] - M * cA2.y * cA2.z, s22 = red[14] - M * cA2.z * cA2.z;
-    const float tr = s00 + s11 + s22;
-    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, sub(La, Lb), om);
-  }
-  const float3 anc = f3(bt[aslot]);
-  bt[4] = make_float4(cA2.x, cA2.y, cA2.z, 0.f);
-  bt[5] = make_float4(dv.x, dv.y, dv.z, 0.f);
-  bt[8] = make_float4(om.x, om.y, om.z, 0.f);
-  const float3 cn = add(add(anc, cA2), mul(sp.dt, dv));   // CoM after the correction
-  bt[nslot] = make_float4(cn.x, cn.y, cn.z, 0.f);
-}
-
-// totals of one body: its chunks' partial sums added in chunk order
-template <int NV>
-__device__ __forceinline__ void body_totals(const float *partials, const BodyRec &br, float *out) {
-  const float *pt = partials + (size_t)kPartialFloats * br.slot0;
-#pragma unroll
-  for (int j = 0; j < NV; ++j) out[j] = pt[j];
-  for (int k = 1; k < br.nk; ++k) {
-    pt += kPartialFloats;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) out[j] += pt[j];
-  }
-}
-
 template <bool kDxShared, bool kVShared, int kMaxThreads, int kMinBlocks>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -191,8 +132,11 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
   float4 *Xs = reinterpret_cast<float4 *>(smem);
   float4 *DXs = kDxShared ? Xs + a.ncap : nullptr;
   unsigned char *build = reinterpret_cast<unsigned char *>(Xs + a.ncap);
-  // velocities of the scene: in shared memory after the DX area, or global
-  float4 *Vsm = kVShared ? Xs + 2 * a.ncap : nullptr;
+  // velocities of the scene: in shared memory after the DX/build area, or global
+  float4 *Vsm = kVShared ? reinterpret_cast<float4 *>(smem + a.v_off) : nullptr;
+  // partial sums of the chunks: in shared memory when the scene has at most
+  // ccap chunks, else in global memory
+  float *part_sm = reinterpret_cast<float *>(smem + a.part_off);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
 
@@ -286,7 +230,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     uint16_t *slist = lbody + ncap_even(a.ncap);                     // [N] interface particles
     uint16_t *sidx = slist + ncap_even(a.ncap);                      // [|S|] sorted by bucket
     uint32_t *start = reinterpret_cast<uint32_t *>(sidx + ncap_even(a.ncap));   // [T+1]
-    uint8_t *cand = reinterpret_cast<uint8_t *>(start + (fused_tcap(a.ncap) + 1));   // [|S|]
+    uint8_t *cand = reinterpret_cast<uint8_t *>(start + (a.tcap + 1));   // [|S|]
     __shared__ uint32_t s_nS;
     if (tid == 0) s_nS = 0;
     for (int bl = warp; bl < B; bl += nwarps) {
@@ -394,8 +338,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     }
     __syncthreads();
     const int32_t nS = (int32_t)s_nS;
+    // bucket table of the interface grid: load factor <= 1/4 where the
+    // class's shared memory allows (fewer hash collisions per search)
     uint32_t T = 1;
-    while (T < (uint32_t)nS) T <<= 1;
+    while (T < (uint32_t)nS * 4u && T < (uint32_t)a.tcap) T <<= 1;
     for (uint32_t k = tid; k <= T; k += nt) start[k] = 0u;
     __syncthreads();
     for (int32_t s = tid; s < nS; s += nt) {
@@ -459,13 +405,22 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       if (cand[s]) Xs[slist[s]].w = -Xs[slist[s]].w;
     __syncthreads();
 
-    // ---- K solver iterations over chunks ------------------------------------
-    // biter per body: [0] rotation, [1] c_bsm - a, [2] P_bsm, [3] L_bsm,
-    // [4] c_asm - a, [5] dv, [6]/[7] the anchor a of even/odd iterations,
-    // [8] w.  Anchors alternate so that a body's next anchor can be written
-    // while its chunks still use the current one.
+    // ---- K solver iterations ---------------------------------------------
+    // (A) contacts per chunk, spread over all warps, each chunk writing its
+    //     partial first body sums;
+    // (B) one owner warp per body (bodies handed out largest first): chunk
+    //     totals in chunk order -> rotation -> goals -> second sums ->
+    //     momentum corrections -> X_{i+1}, V_{i+1}.
+    // Every contact reads X_i before the barrier that ends (A), so the
+    // owners may then overwrite positions (Jacobi order of Alg. 1).
+    // biter per body: [0] rotation (warm start), [6] anchor of the FP32 sums.
     const Chunk *ch = a.chunks + sp.c0;
     const int NC = sp.nc;
+    const int32_t *order = a.border + b0;
+    // partial-sum slots: local chunk numbering in shared memory, or the
+    // global slots of the bodies
+    const bool part_local = NC <= a.ccap;
+    const int32_t slot_base = a.bodies[b0].slot0;   // slots of a scene are contiguous
     for (int bl = tid; bl < B; bl += nt) {
       float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
       bt[0] = a.quat[b0 + bl];
@@ -475,14 +430,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     const float r = sp.radius, dc = 2.f * r, mu = sp.friction;
     const float3 nrm = make_float3(sp.nx, sp.ny, sp.nz);
     for (int it = 0; it < sp.iterations; ++it) {
-      const int aslot = 6 + (it & 1), nslot = 6 + ((it + 1) & 1);
-      // (A) contacts from X_i (Jacobi) and the first body sums, per chunk;
-      // each lane owns up to kChunk/32 = 4 particles of the chunk
       for (int c = warp; c < NC; c += nwarps) {
         const Chunk C = ch[c];
         const BodyRec br = a.bodies[C.body];
-        const float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
-        const float3 anc = f3(bt[aslot]);
+        const float3 anc = f3(a.biter[(size_t)kBodyScratch * C.body + 6]);
         const int32_t l0 = C.first - p0, l1 = l0 + C.count;
         float4 q4[kChunk / 32];
 #pragma unroll
@@ -529,7 +480,11 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           }
           DX[i] = make_float4(dX.x, dX.y, dX.z, 0.f);
           const float3 xb = add(f3(xp), dX);
-          const float3 vb = std_vel ? mul(idt, sub(xb, f3(a.X[p]))) : add(f3(vp), mul(idt, dX));
+          float3 vb;
+          if (std_vel)   // uniform per scene
+            vb = mul(idt, sub(xb, f3(a.X[p])));
+          else
+            vb = add(f3(vp), mul(idt, dX));
           const float4 q = q4[j];
           const float m = q.w;
           const float3 e = sub(xb, anc);
@@ -545,58 +500,73 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
 #pragma unroll
         for (int k = 0; k < 18; ++k) red[k] = wsum(red[k]);
         if (lane == 0) {
-          float *pt = a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
+          float *pt = part_local ? part_sm + kPartialFloats * (br.slot0 - slot_base + C.k)
+                                 : a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
 #pragma unroll
           for (int k = 0; k < 18; ++k) pt[k] = red[k];
         }
       }
-      __syncthreads();
-      // (A2) one thread per body: totals over the body's chunks (chunk order)
-      // and the rotation of the shape-matching fit
-      for (int bl = tid; bl < B; bl += nt) {
-        const BodyRec br = a.bodies[b0 + bl];
-        float red[18];
-        body_totals<18>(a.partials, br, red);
-        body_rotation(red, br, a.biter + (size_t)kBodyScratch * (b0 + bl));
-      }
-      __syncthreads();
-      // (B) shape-matching goals g = R q + c -> X_asm, V_asm and the second sums
-      for (int c = warp; c < NC; c += nwarps) {
-        const Chunk C = ch[c];
-        const BodyRec br = a.bodies[C.body];
-        const float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
-        const float3 anc = f3(bt[aslot]);
-        float R[9];
-        quat_mat(bt[0], R);
-        const float3 cA = f3(bt[1]);
-        const int32_t l0 = C.first - p0, l1 = l0 + C.count;
-        float4 q4[kChunk / 32];
+      __syncthreads();   // every contact of this iteration has read X_i
+      for (int o = warp; o < B; o += nwarps) {
+        const int32_t b = order[o];
+        const BodyRec br = a.bodies[b];
+        float4 *bt = a.biter + (size_t)kBodyScratch * b;
+        const float3 anc = f3(bt[6]);
+        // first sums: the chunks' partials in chunk order (lane j adds value j)
+        float red1[18];
+        {
+          float mine = 0.f;
+          if (lane < 18) {
+            const float *pt = (part_local ? part_sm + kPartialFloats * (br.slot0 - slot_base)
+                                          : a.partials + (size_t)kPartialFloats * br.slot0) + lane;
+            mine = pt[0];
+            for (int k = 1; k < br.nk; ++k) mine += pt[(size_t)kPartialFloats * k];
+          }
 #pragma unroll
-        for (int j = 0; j < kChunk / 32; ++j) {
-          const int32_t i = l0 + lane + 32 * j;
-          if (i < l1) q4[j] = __ldg(a.Q + p0 + i);
+          for (int j = 0; j < 18; ++j) red1[j] = __shfl_sync(kFull, mine, j);
         }
+        const float M = br.mass, iM = br.inv_mass;
+        const float3 cA = mul(iM, make_float3(red1[0], red1[1], red1[2]));
+        const float3 Pb = make_float3(red1[12], red1[13], red1[14]);
+        const float3 Lb = sub(make_float3(red1[15], red1[16], red1[17]), cross3(cA, Pb));
+        float Am[9];
+        {
+          const float qs[3] = {br.qsx, br.qsy, br.qsz};
+          const float ca[3] = {cA.x, cA.y, cA.z};
+#pragma unroll
+          for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Am[3 * rr + cc] = red1[3 + 3 * rr + cc] - ca[rr] * qs[cc];
+        }
+        const float4 qrot = shape_rotation(Am, bt[0]);
+        float R[9];
+        quat_mat(qrot, R);
+        // goals g = R q + c -> X_asm, V_asm; second sums
+        const int32_t l0 = br.start - p0, l1 = l0 + br.count;
         float red[15];
 #pragma unroll
         for (int k = 0; k < 15; ++k) red[k] = 0.f;
-#pragma unroll
-        for (int j = 0; j < kChunk / 32; ++j) {
-          const int32_t i = l0 + lane + 32 * j;
-          if (i >= l1) continue;
+        for (int32_t i = l0 + lane; i < l1; i += 32) {
           const int32_t p = p0 + i;
           const float4 xi = Xs[i];
           const float3 dX = f3(DX[i]);
           const float4 vi = Vl[i];
-          const float4 q = q4[j];
+          const float4 q = __ldg(a.Q + p);
           const float m = q.w;
           const float3 xb = add(f3(xi), dX);
-          const float3 vb = std_vel ? mul(idt, sub(xb, f3(a.X[p]))) : add(f3(vi), mul(idt, dX));
+          float3 vb, xinit = make_float3(0.f, 0.f, 0.f);
+          if (std_vel) {
+            xinit = f3(a.X[p]);
+            vb = mul(idt, sub(xb, xinit));
+          } else {
+            vb = add(f3(vi), mul(idt, dX));
+          }
           const float3 grel = add(make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z,
                                               R[3] * q.x + R[4] * q.y + R[5] * q.z,
                                               R[6] * q.x + R[7] * q.y + R[8] * q.z), cA);
           const float3 dsm = sub(grel, sub(xb, anc));
           const float3 xa = add(xb, dsm);
-          const float3 va = std_vel ? mul(idt, sub(xa, f3(a.X[p]))) : add(vb, mul(idt, dsm));
+          const float3 va = std_vel ? mul(idt, sub(xa, xinit)) : add(vb, mul(idt, dsm));
           DX[i] = make_float4(xa.x, xa.y, xa.z, 0.f);
           Vl[i] = make_float4(va.x, va.y, va.z, 0.f);
           const float3 e = sub(xa, anc);
@@ -610,29 +580,20 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         }
 #pragma unroll
         for (int k = 0; k < 15; ++k) red[k] = wsum(red[k]);
-        if (lane == 0) {
-          float *pt = a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
-#pragma unroll
-          for (int k = 0; k < 15; ++k) pt[k] = red[k];
+        // momentum enforcement (Sec. III-C)
+        const float3 cA2 = mul(iM, make_float3(red[0], red[1], red[2]));
+        const float3 Pa = make_float3(red[3], red[4], red[5]);
+        const float3 La = sub(make_float3(red[6], red[7], red[8]), cross3(cA2, Pa));
+        float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
+        if (!(sp.flags & kNoLinMom)) dv = mul(iM, sub(Pb, Pa));
+        if (!(sp.flags & kNoAngMom)) {
+          const float s00 = red[9] - M * cA2.x * cA2.x, s01 = red[10] - M * cA2.x * cA2.y,
+                      s02 = red[11] - M * cA2.x * cA2.z, s11 = red[12] - M * cA2.y * cA2.y,
+                      s12 = red[13] - M * cA2.y * cA2.z, s22 = red[14] - M * cA2.z * cA2.z;
+          const float tr = s00 + s11 + s22;
+          solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, sub(La, Lb), om);
         }
-      }
-      __syncthreads();
-      // (B2) one thread per body: momentum corrections
-      for (int bl = tid; bl < B; bl += nt) {
-        const BodyRec br = a.bodies[b0 + bl];
-        float red[15];
-        body_totals<15>(a.partials, br, red);
-        body_momentum(red, br, a.biter + (size_t)kBodyScratch * (b0 + bl), aslot, nslot, sp);
-      }
-      __syncthreads();
-      // (C) uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
-      for (int c = warp; c < NC; c += nwarps) {
-        const Chunk C = ch[c];
-        const float4 *bt = a.biter + (size_t)kBodyScratch * C.body;
-        const float3 anc = f3(bt[aslot]);
-        const float3 cA2 = f3(bt[4]), dv = f3(bt[5]), om = f3(bt[8]);
         bool bad = false;
-        const int32_t l0 = C.first - p0, l1 = l0 + C.count;
         for (int32_t i = l0 + lane; i < l1; i += 32) {
           const float3 xa = f3(DX[i]);
           const float3 va = f3(Vl[i]);
@@ -644,6 +605,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           Vl[i] = make_float4(v.x, v.y, v.z, 0.f);
           bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
         }
+        __syncwarp();
+        if (lane == 0) {
+          bt[0] = qrot;
+          const float3 cn = add(add(anc, cA2), mul(dt, dv));   // CoM after the correction
+          bt[6] = make_float4(cn.x, cn.y, cn.z, 0.f);
+        }
         if (__any_sync(kFull, bad) && lane == 0) atomicOr(&a.scene_err[sid], (uint32_t)PBDR_EBIT_NONFINITE);
       }
       __syncthreads();
@@ -651,7 +618,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     for (int bl = tid; bl < B; bl += nt) {
       const float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
       a.quat[b0 + bl] = bt[0];
-      a.bcom[b0 + bl] = bt[6 + (sp.iterations & 1)];
+      a.bcom[b0 + bl] = bt[6];
     }
     // ---- write the substep's positions back ------------------------------
     for (int32_t i = tid; i < N; i += nt) {
@@ -665,15 +632,22 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
 
 }  // namespace
 
-size_t fused_smem_bytes(int ncap, bool dx_shared, bool v_shared) {
-  // X (16 B per particle) + max(DX 16 B per particle, neighbour build area:
-  // lbody, interface list, sorted list (u16 each), bucket starts u32[T+1]
-  // with T <= the smallest power of two >= ncap)
-  size_t pad = ((size_t)ncap + 7) & ~(size_t)7;
-  const size_t tcap = (size_t)fused_tcap(ncap);
-  size_t build = 3 * 2 * pad + 4 * (tcap + 1) + pad;   // + candidate flags
-  size_t dxa = dx_shared ? 16 * (size_t)ncap : 0;
-  return 16 * (size_t)ncap + (dxa > build ? dxa : build) + (v_shared ? 16 * (size_t)ncap : 0);
+// shared-memory layout of a class: Xs | DX or build area | V | partials
+FusedLayout fused_layout(int ncap, bool dx_shared, bool v_shared, bool part_shared) {
+  FusedLayout L{};
+  const size_t pad = ((size_t)ncap + 7) & ~(size_t)7;
+  L.tcap = dx_shared ? 2 * fused_tcap(ncap) : fused_tcap(ncap);
+  const size_t build = 7 * pad + 4 * ((size_t)L.tcap + 1);   // lbody, slist, sidx, cand + starts
+  const size_t dxa = dx_shared ? 16 * (size_t)ncap : 0;
+  size_t off = 16 * (size_t)ncap + (dxa > build ? dxa : build);
+  off = (off + 15) & ~(size_t)15;
+  L.v_off = v_shared ? off : 0;
+  if (v_shared) off += 16 * (size_t)ncap;
+  L.ccap = part_shared ? ncap / 16 : 0;
+  L.part_off = off;
+  off += (size_t)L.ccap * kPartialFloats * sizeof(float);
+  L.bytes = off;
+  return L;
 }
 
 // kernel variant for a launch: <= 256 threads with registers capped for
@@ -691,7 +665,7 @@ static void *pick(bool dx, bool v, int threads) {
 int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s) {
   if (a.nscenes <= 0) return 0;
   const bool dxs = a.dx_scratch == nullptr;
-  const size_t smem = fused_smem_bytes(a.ncap, dxs, a.v_shared != 0);
+  const size_t smem = a.smem_bytes;
   void *fn = pick(dxs, a.v_shared != 0, threads);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   FusedArgs arg = a;
@@ -701,7 +675,7 @@ int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s) {
 }
 
 int fused_max_blocks_per_sm(int ncap, bool dx_shared, bool v_shared, int threads) {
-  const size_t smem = fused_smem_bytes(ncap, dx_shared, v_shared);
+  const size_t smem = fused_layout(ncap, dx_shared, v_shared, dx_shared).bytes;
   void *fn = pick(dx_shared, v_shared, threads);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;

@@ -143,6 +143,7 @@ struct FusedArgs {
   float4 *quat, *bcom;     // per-body warm start and sum anchor, updated
   float4 *biter;           // per-body scratch: kBodyScratch float4 per body
   const Chunk *chunks;     // all chunks (scenes index them through c0, nc)
+  const int32_t *border;   // per scene (at b0): its bodies, largest first
   float *partials;         // kPartialFloats per slot
   float4 *dx_scratch;      // global dX / x_asm scratch, or nullptr (shared memory)
   int32_t *nbr_cnt, *nbr;
@@ -155,6 +156,16 @@ struct FusedArgs {
   int32_t ncap;            // particle capacity of the class
   int32_t grid;
   int32_t v_shared;        // velocities held in shared memory during the substep
+  int32_t tcap;            // largest bucket table of the interface grid
+  int32_t ccap;            // chunks whose partial sums fit in shared memory
+  size_t v_off, part_off;  // shared-memory offsets of V and of the partial sums
+  size_t smem_bytes;
+};
+
+// shared-memory layout of a size class of the scene-resident kernel
+struct FusedLayout {
+  int32_t tcap, ccap;
+  size_t v_off, part_off, bytes;
 };
 
 struct WrenchArgs {
@@ -183,7 +194,7 @@ int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_wrench(const WrenchArgs &a, cudaStream_t s);
 int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
 int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s);
-size_t fused_smem_bytes(int ncap, bool dx_shared, bool v_shared);
+FusedLayout fused_layout(int ncap, bool dx_shared, bool v_shared, bool part_shared);
 int fused_max_blocks_per_sm(int ncap, bool dx_shared, bool v_shared, int threads);
 
 // Stable LSD radix sort of (key, value) pairs, keys < 2^bits.  Buffers:
