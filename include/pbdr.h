@@ -183,15 +183,17 @@ int pbdr_read_neighbors(pbdr_ctx *ctx, pbdr_scene scene, uint32_t *sorted_key,
  *   legacy NULL stream, and not while stage timing is on); 0 = plain launches.
  * PBDR_OPT_AUTOTUNE: 1 (default) = the first pbdr_step of a scene set times
  *   the scene-resident kernel's launch shapes per size class (threads per CTA,
- *   velocities in shared memory, CTAs per SM) on substeps whose effects are
- *   undone, and keeps the fastest; results do not depend on the shape. */
+ *   scratch and velocities in shared or global memory, CTAs per SM) on whole
+ *   substeps whose effects are undone, and keeps the fastest; results do not
+ *   depend on the shape. */
 #define PBDR_OPT_GRAPHS 3
 #define PBDR_OPT_AUTOTUNE 4
 int pbdr_set_option(pbdr_ctx *ctx, int32_t option, int64_t value);
 
 /* Launch shapes of the scene-resident kernel for the scene set ids[0..n):
- * out[5k..5k+4] = {particle capacity, scenes, threads per CTA, velocities in
- * shared memory (0/1), CTAs} for size class k = 0..3 (cap >= 20). */
+ * out[5k..5k+4] = {particle capacity, scenes, threads per CTA, scratch bits
+ * (1: velocities in shared memory, 2: per-particle scratch in shared memory),
+ * CTAs} for size class k = 0..3 (cap >= 20). */
 int pbdr_plan_config(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int32_t *out, int32_t cap);
 
 /* Launch statistics of the last pbdr_step call: the number of kernel

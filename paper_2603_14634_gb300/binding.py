@@ -244,7 +244,7 @@ def pbdr_plan_config(ctx: int, ids: Sequence[int]):
     arr, p = _ids(ids)
     out = np.zeros(20, np.int32)
     _check(load().pbdr_plan_config(ctx, p, len(arr), _ptr(out), 20))
-    keys = ("capacity", "scenes", "threads", "v_shared", "ctas")
+    keys = ("capacity", "scenes", "threads", "scratch_bits", "ctas")
     return [dict(zip(keys, map(int, out[5 * k:5 * k + 5]))) for k in range(4)]
 
 

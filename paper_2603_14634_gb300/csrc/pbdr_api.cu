@@ -593,14 +593,19 @@ int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   return PBDR_OK;
 }
 
-// Autotuner of the scene-resident kernel: for every size class, times the
-// candidate launch shapes (threads per CTA, velocities in shared memory or
-// not, CTAs per SM) on class-only substeps and keeps the fastest.  The
-// kernel's results do not depend on its launch shape, and the state the
-// trial substeps change is saved before and restored after, so tuning has
-// no effect on the simulation.
+// Autotuner of the scene-resident kernel.  The candidate launch shapes of a
+// size class are: threads per CTA (128, 256, 512), the per-particle scratch
+// (dX, x_asm) in shared or in global memory, velocities in shared memory or
+// not, and the CTAs kept per SM (the occupancy limit or half of it).  Classes
+// are tuned one after the other (largest work first) by timing whole
+// substeps of the plan - all classes running concurrently as in production -
+// with the other classes at their current shapes, and each keeps its fastest
+// shape.  The kernel's results do not depend on its launch shape, and the
+// state the trial substeps change is saved before and restored after, so
+// tuning has no effect on the simulation.
 int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
   int rc;
+  if (!c->dx_scratch.p && (rc = dev_alloc(c, c->dx_scratch, (size_t)c->pcap * sizeof(float4)))) return rc;
   const size_t nX = (size_t)std::max(c->np_used, 1) * sizeof(float4);
   const size_t nB = (size_t)std::max(c->nb_used, 1) * sizeof(float4);
   const size_t nE = (size_t)std::max<size_t>(c->sh.size(), 1) * sizeof(uint32_t);
@@ -616,45 +621,64 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
+  auto time_substeps = [&](float *ms) -> int {
+    int64_t l = 0;
+    int r2 = fused_substep(c, P, s, l);   // warm
+    if (r2) return r2;
+    CUDA_TRY(cudaEventRecord(e0, s));
+    for (int rep = 0; rep < 2; ++rep)
+      if ((r2 = fused_substep(c, P, s, l))) return r2;
+    CUDA_TRY(cudaEventRecord(e1, s));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return PBDR_OK;
+  };
+  // classes by descending particle count
+  std::vector<std::pair<int64_t, int>> work;
   for (int k = 0; k < (int)P.classes.size(); ++k) {
-    Plan::FClass &F = P.classes[k];
-    if (!F.n) continue;
-    const int threads_c[3] = {128, 256, 512};
+    int64_t w = 0;
+    for (int32_t id : P.classes[k].ids) w += c->sh[id].np;
+    if (P.classes[k].n) work.push_back({-w, k});
+  }
+  std::sort(work.begin(), work.end());
+  for (auto &wk : work) {
+    Plan::FClass &F = P.classes[wk.second];
     float best = 1e30f;
     int bt = F.threads, bg = F.grid;
-    bool bv = F.v_shared;
-    for (int ti = 0; ti < 3; ++ti) {
+    bool bv = F.v_shared, bd = F.dx_shared;
+    const int threads_c[3] = {128, 256, 512};
+    for (int dxi = 0; dxi < 2; ++dxi) {
+      const bool dxs = dxi == 0;
+      if (dxs && fused_layout(F.ncap, true, false, true).bytes > 220 * 1024) continue;
       for (int vs = 0; vs < 2; ++vs) {
         const bool vsh = vs == 1;
-        if (vsh && !(F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024)) continue;
-        const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, vsh, threads_c[ti]);
-        if (per_sm < 1) continue;
-        const int cps_c[2] = {per_sm, std::max(1, per_sm / 2)};
-        for (int ci = 0; ci < (per_sm > 1 ? 2 : 1); ++ci) {
-          F.threads = threads_c[ti];
-          F.v_shared = vsh;
-          F.grid = std::min<int>(F.n, cps_c[ci] * c->num_sms);
-          for (int rep = 0; rep < 3; ++rep) {
-            if (rep == 1) CUDA_TRY(cudaEventRecord(e0, s));
-            CUDA_TRY(cudaMemsetAsync(c->tickets.as<uint32_t>() + k, 0, 4, s));
-            launch_class(c, P, k, s);
-          }
-          CUDA_TRY(cudaEventRecord(e1, s));
-          CUDA_TRY(cudaEventSynchronize(e1));
-          CUDA_TRY(cudaGetLastError());
-          float ms = 0.f;
-          CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < best) {
-            best = ms;
-            bt = F.threads;
-            bv = F.v_shared;
-            bg = F.grid;
+        if (vsh && !(dxs && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024)) continue;
+        for (int ti = 0; ti < 3; ++ti) {
+          const int per_sm = fused_max_blocks_per_sm(F.ncap, dxs, vsh, threads_c[ti]);
+          if (per_sm < 1) continue;
+          const int cps_c[2] = {per_sm, std::max(1, per_sm / 2)};
+          for (int ci = 0; ci < (per_sm > 1 ? 2 : 1); ++ci) {
+            F.threads = threads_c[ti];
+            F.dx_shared = dxs;
+            F.v_shared = vsh;
+            F.grid = std::min<int>(F.n, cps_c[ci] * c->num_sms);
+            float ms = 0.f;
+            if ((rc = time_substeps(&ms))) return rc;
+            if (ms < best) {
+              best = ms;
+              bt = F.threads;
+              bv = F.v_shared;
+              bd = F.dx_shared;
+              bg = F.grid;
+            }
           }
         }
       }
     }
     F.threads = bt;
     F.v_shared = bv;
+    F.dx_shared = bd;
     F.grid = bg;
   }
   cudaEventDestroy(e0);
@@ -1307,7 +1331,7 @@ int pbdr_plan_config(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t *out
     out[5 * k + 0] = has ? P->classes[k].ncap : 0;
     out[5 * k + 1] = has ? P->classes[k].n : 0;
     out[5 * k + 2] = has ? P->classes[k].threads : 0;
-    out[5 * k + 3] = has ? (P->classes[k].v_shared ? 1 : 0) : 0;
+    out[5 * k + 3] = has ? ((P->classes[k].v_shared ? 1 : 0) | (P->classes[k].dx_shared ? 2 : 0)) : 0;
     out[5 * k + 4] = has ? P->classes[k].grid : 0;
   }
   return PBDR_OK;
