@@ -56,6 +56,11 @@ def parse_args():
     ap.add_argument("--cpu-substeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample-scenes", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="length of the Poisson arrival trace of the serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-pool", type=int, default=32)
+    ap.add_argument("--serve-budget-gb", type=int, default=120)
     ap.add_argument("--settle", type=int, default=240,
                     help="substeps run before the warm-up so that bodies have landed and touch")
     a = ap.parse_args()
@@ -415,6 +420,8 @@ def run_pbdr(args, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
     }
+    if world == 1 and args.serve_seconds > 0:
+        line["serving"] = run_serving(args, local_rank)
     if world == 1 and not args.no_cpu_baseline:
         cpu_scs = scs[: args.cpu_scenes]
         thr = host_cores()
@@ -427,6 +434,43 @@ def run_pbdr(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+def run_serving(args, local_rank):
+    """Serving: Poisson arrivals of scene requests (1e3-2e5 particles, bodies
+    of 64-512 particles, 1-100 substeps each) drawn from a seeded pool,
+    admitted by an HBM budget and served by continuous batching."""
+    import numpy as np
+    import torch
+    from paper_2603_14634_gb300 import scenes
+    from paper_2603_14634_gb300.serve import Server, poisson_trace
+    rng = np.random.default_rng(args.seed + 1000)
+    pool = [scenes.serving_request(rng)[0] for _ in range(args.serve_pool)]
+    arrivals = poisson_trace(args.serve_rate, args.serve_seconds, seed=args.seed)
+    pick = rng.integers(0, len(pool), size=len(arrivals))
+    steps = rng.integers(1, 101, size=len(arrivals))
+    stream = torch.cuda.Stream()
+    srv = Server(hbm_budget_bytes=args.serve_budget_gb << 30, device=local_rank,
+                 stream=stream.cuda_stream)
+    offered = 0
+    for t, k, st in zip(arrivals, pick, steps):
+        srv.submit(pool[k], int(st), arrival=float(t))
+        offered += pool[k].num_particles * pool[k].iterations * int(st)
+    with torch.cuda.stream(stream):
+        stats = srv.run(realtime=True)
+    errs = sum(1 for r in srv.results.values() if r[2])
+    return {
+        "requests": stats["requests"], "arrival_rate_hz": args.serve_rate,
+        "trace_s": args.serve_seconds, "budget_gb": args.serve_budget_gb,
+        "request_latency_ms_p50": round(stats["latency_ms_p50"], 3),
+        "request_latency_ms_p99": round(stats["latency_ms_p99"], 3),
+        "tick_ms_p50": round(stats["tick_ms_p50"], 3), "tick_ms_p99": round(stats["tick_ms_p99"], 3),
+        "offered_particle_iters_per_s": round(offered / args.serve_seconds, 1),
+        "achieved_particle_iters_per_s": round(stats["achieved_particle_iters_per_s"], 1),
+        "wall_s": round(stats["wall_s"], 3), "requests_with_error_bits": errs,
+        "ms_per_tick_split": {k: round(v, 3) for k, v in stats["host_ms_per_tick"].items()},
+        "what": "continuous batching: admit between substeps by HBM budget, one batched substep of all resident requests per tick, retire and free finished ones",
+    }
 
 
 def run_reference(args, rank):

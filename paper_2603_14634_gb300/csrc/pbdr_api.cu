@@ -58,11 +58,47 @@ uint32_t table_size(int32_t n) {
   return t;
 }
 
+// First-fit allocator of index ranges of the packed particle, body and chunk
+// tables: destroyed scenes return their ranges, new scenes reuse them.
+struct RangeAlloc {
+  int32_t top = 0;                      // high-water mark
+  std::map<int32_t, int32_t> free_;     // start -> length
+  int32_t take(int32_t n) {             // first fit, or -1
+    if (n <= 0) return top;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        const int32_t st = it->first, len = it->second;
+        free_.erase(it);
+        if (len > n) free_[st + n] = len - n;
+        return st;
+      }
+    }
+    return -1;
+  }
+  void give(int32_t st, int32_t n) {
+    if (n <= 0) return;
+    auto it = free_.emplace(st, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
 struct SceneHost {
   bool alive = false;
   int32_t p0 = 0, np = 0, b0 = 0, nb = 0;
   ScenePar par{};
   int wrench_bodies = 0;
+  int32_t c0 = 0, nc = 0;          // chunk range
 };
 
 struct Plan {
@@ -117,7 +153,8 @@ struct pbdr_ctx {
   size_t budget = 0;
   size_t used = 0;
   int32_t pcap = 0, bcap = 0, scap = 0;
-  int32_t np_used = 0, nb_used = 0;
+  int32_t np_used = 0, nb_used = 0;   // high-water marks of the packed tables
+  RangeAlloc pa, ba, ca;               // free ranges of particles, bodies, chunks
   int nbr_cap = 32;
   DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
   DevBuf bodies, wrench, quat, bcom, biter, border;
@@ -909,11 +946,30 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
         return fail(PBDR_ERR_INVALID, "positions and velocities must be finite");
     }
   }
-  if ((int64_t)c->np_used + N > INT32_MAX / 2 || (int64_t)c->nb_used + B > INT32_MAX / 2)
+  if ((int64_t)c->pa.top + N > INT32_MAX / 2 || (int64_t)c->ba.top + B > INT32_MAX / 2)
     return fail(PBDR_ERR_INVALID, "context particle or body count overflow");
-  const int32_t sid = (int32_t)c->sh.size();
+  // scene id: the first destroyed slot, else a new one
+  int32_t sid = (int32_t)c->sh.size();
+  for (int32_t i = 0; i < (int32_t)c->sh.size(); ++i)
+    if (!c->sh[i].alive) {
+      sid = i;
+      break;
+    }
   const int32_t old_pcap = c->pcap;
   // work chunks of the scene-resident kernel: up to kChunk particles of one body
+  int32_t nchunks = 0;
+  for (int32_t b = 0; b < B; ++b) nchunks += (d->body_off[b + 1] - d->body_off[b] + kChunk - 1) / kChunk;
+  // ranges of the packed tables: reuse freed ranges first (first fit)
+  int32_t P0 = c->pa.take(N), B0 = c->ba.take(B), C0 = c->ca.take(nchunks);
+  const bool p_top = P0 < 0, b_top = B0 < 0, c_top = C0 < 0;
+  if (p_top) P0 = c->pa.top;
+  if (b_top) B0 = c->ba.top;
+  if (c_top) C0 = c->ca.top;
+  auto give_back = [&]() {
+    if (!p_top) c->pa.give(P0, N);
+    if (!b_top) c->ba.give(B0, B);
+    if (!c_top) c->ca.give(C0, nchunks);
+  };
   std::vector<Chunk> chk;
   int32_t multi = 0;
   for (int32_t b = 0; b < B; ++b) {
@@ -921,12 +977,15 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     const int32_t nk = (n + kChunk - 1) / kChunk;
     multi += nk > 1;
     for (int32_t k = 0; k < nk; ++k)
-      chk.push_back(Chunk{c->nb_used + b, c->np_used + d->body_off[b] + k * kChunk,
-                          std::min(kChunk, n - k * kChunk), k});
+      chk.push_back(Chunk{B0 + b, P0 + d->body_off[b] + k * kChunk, std::min(kChunk, n - k * kChunk), k});
   }
   std::stable_sort(chk.begin(), chk.end(), [](const Chunk &x, const Chunk &y) { return x.count > y.count; });
-  int rc = ensure_capacity(c, c->np_used + N, c->nb_used + B, sid + 1, c->nc_used + (int32_t)chk.size());
-  if (rc) return rc;
+  int rc = ensure_capacity(c, std::max(c->pa.top, P0 + N), std::max(c->ba.top, B0 + B),
+                           std::max((int32_t)c->sh.size(), sid + 1), std::max(c->ca.top, C0 + nchunks));
+  if (rc) {
+    give_back();
+    return rc;
+  }
   if (c->pcap != old_pcap) invalidate_plans(c);
 
   // host-side FP64 rest shape (Mueller et al. 2005): M, c0, q = x0 - c0
@@ -934,7 +993,7 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   std::vector<int32_t> pb(N);
   std::vector<BodyRec> br(B);
   std::vector<float4> com(B);
-  int32_t slot_next = c->nc_used;
+  int32_t slot_next = C0;
   for (int32_t b = 0; b < B; ++b) {
     const int32_t s0 = d->body_off[b], s1 = d->body_off[b + 1];
     double M = 0, cx = 0, cy = 0, cz = 0;
@@ -961,13 +1020,13 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
       qs[2] += md * q.z;
       X[p] = make_float4(d->pos[3 * p], d->pos[3 * p + 1], d->pos[3 * p + 2], d->inv_mass[p]);
       V[p] = make_float4(d->vel[3 * p], d->vel[3 * p + 1], d->vel[3 * p + 2], 0.f);
-      pb[p] = c->nb_used + b;
+      pb[p] = B0 + b;
     }
     BodyRec &r = br[b];
     r.slot0 = slot_next;
     r.nk = (s1 - s0 + kChunk - 1) / kChunk;
     slot_next += r.nk;
-    r.start = c->np_used + s0;
+    r.start = P0 + s0;
     r.count = s1 - s0;
     r.scene = sid;
     r.has_wrench = 0;
@@ -979,9 +1038,11 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   }
   SceneHost S;
   S.alive = true;
-  S.p0 = c->np_used;
+  S.p0 = P0;
   S.np = N;
-  S.b0 = c->nb_used;
+  S.b0 = B0;
+  S.c0 = C0;
+  S.nc = nchunks;
   S.nb = B;
   ScenePar &P = S.par;
   P.radius = d->radius;
@@ -1005,7 +1066,7 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   P.iterations = d->iterations;
   P.flags = d->flags;
   P.T = table_size(N);
-  P.c0 = c->nc_used;
+  P.c0 = C0;
   P.nc = (int32_t)chk.size();
   P.multi_chunk_bodies = multi;
   P.pad = 0;
@@ -1027,23 +1088,33 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + S.b0, wr.data(), (size_t)B * sizeof(BodyWrench), cudaMemcpyHostToDevice));
   }
   if (!chk.empty())
-    CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + c->nc_used, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + C0, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
   if (B > 0) {   // the scene's bodies, largest first (owner-warp order of the scene-resident kernel)
     std::vector<int32_t> ord(B);
-    for (int32_t b = 0; b < B; ++b) ord[b] = c->nb_used + b;
+    for (int32_t b = 0; b < B; ++b) ord[b] = B0 + b;
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
-      return br[x - c->nb_used].count > br[y - c->nb_used].count;
+      return br[x - B0].count > br[y - B0].count;
     });
-    CUDA_TRY(cudaMemcpy(c->border.as<int32_t>() + c->nb_used, ord.data(), (size_t)B * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->border.as<int32_t>() + B0, ord.data(), (size_t)B * 4, cudaMemcpyHostToDevice));
   }
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
-  c->bh.insert(c->bh.end(), br.begin(), br.end());
-  c->wh.insert(c->wh.end(), wr.begin(), wr.end());
-  c->sh.push_back(S);
-  c->np_used += N;
-  c->nb_used += B;
-  c->nc_used += (int32_t)chk.size();
+  if ((int32_t)c->bh.size() < B0 + B) {
+    c->bh.resize(B0 + B);
+    c->wh.resize(B0 + B);
+  }
+  std::copy(br.begin(), br.end(), c->bh.begin() + B0);
+  std::copy(wr.begin(), wr.end(), c->wh.begin() + B0);
+  if (sid == (int32_t)c->sh.size())
+    c->sh.push_back(S);
+  else
+    c->sh[sid] = S;
+  if (p_top) c->pa.top = P0 + N;
+  if (b_top) c->ba.top = B0 + B;
+  if (c_top) c->ca.top = C0 + nchunks;
+  c->np_used = c->pa.top;
+  c->nb_used = c->ba.top;
+  c->nc_used = c->ca.top;
   // plans hold per-scene tables sized by the scene count
   invalidate_plans(c);
   *out = sid;
@@ -1054,7 +1125,11 @@ int pbdr_destroy_scene(pbdr_ctx *c, pbdr_scene s) {
   g_err.clear();
   int rc = check_scene(c, s);
   if (rc) return rc;
-  c->sh[s].alive = false;
+  SceneHost &S = c->sh[s];
+  S.alive = false;
+  c->pa.give(S.p0, S.np);
+  c->ba.give(S.b0, S.nb);
+  c->ca.give(S.c0, S.nc);
   invalidate_plans(c);
   return PBDR_OK;
 }

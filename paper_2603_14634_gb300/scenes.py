@@ -327,12 +327,43 @@ def analytic_box(test: int, n: int = 4, box_mass: float = 4.0, spacing: float = 
     return sc
 
 
+def lattice_placement(rng: np.random.Generator, lattice_sizes: Sequence[int], *,
+                      spacing: float = 0.1, radius: float = 0.05, vmax: float = 1.0,
+                      wmax: float = 2.0, z0: float = 0.0):
+    """Fast non-overlapping placement for large requests: bodies go to the
+    cells of a cubic lattice whose pitch is the largest bounding diameter
+    (+2r), in random order, each with a uniform random rotation and a random
+    shift within its cell's slack; the lattice's base rests at height z0.
+    Velocities as in place_bodies."""
+    halfs = [(n - 1) / 2.0 * spacing for n in lattice_sizes]
+    brad = max(math.sqrt(3.0) * h + radius for h in halfs)
+    pitch = 2.0 * brad + 2.0 * radius
+    nb = len(lattice_sizes)
+    side = int(math.ceil(nb ** (1.0 / 3.0)))
+    cells = rng.permutation(side ** 3)[:nb]
+    Rs = random_rotations(rng, nb)
+    pos, vel = [], []
+    for k, n in enumerate(lattice_sizes):
+        c = cells[k]
+        ijk = np.array([c % side, (c // side) % side, c // (side * side)], dtype=np.float64)
+        my = math.sqrt(3.0) * halfs[k] + radius
+        slack = max(0.0, brad - my)
+        ctr = (ijk - (side - 1) / 2.0) * pitch + (rng.random(3) * 2 - 1) * slack
+        ctr[2] += z0 + (side - 1) / 2.0 * pitch + brad
+        p = lattice_cube(n, spacing) @ Rs[k].T + ctr
+        v = (rng.random(3) * 2 - 1) * vmax
+        w = (rng.random(3) * 2 - 1) * wmax
+        pos.append(p)
+        vel.append(v[None, :] + np.cross(w[None, :], p - ctr[None, :]))
+    return pos, vel
+
+
 def serving_request(rng: np.random.Generator, min_particles: int = 1000,
                     max_particles: int = 200000, iterations: int = 10,
                     dt: float = 1.0 / 240.0, friction: float = 0.5):
     """One serving request: particle target P log-uniform in [1e3, 2e5]; n^3
-    bodies with n ~ U{4..8} added until >= P, placed in a box of edge
-    2 (N/8000)^(1/3) m; returns (scene, steps) with steps ~ U{1..100}."""
+    bodies with n ~ U{4..8} (64-512 particles) added until >= P, placed by
+    lattice_placement; returns (scene, steps) with steps ~ U{1..100}."""
     P = math.exp(math.log(min_particles) + rng.random() *
                  (math.log(max_particles) - math.log(min_particles)))
     sizes, total = [], 0
@@ -340,9 +371,7 @@ def serving_request(rng: np.random.Generator, min_particles: int = 1000,
         n = int(rng.integers(4, 9))
         sizes.append(n)
         total += n ** 3
-    edge = 2.0 * (total / 8000.0) ** (1.0 / 3.0)
-    pos, vel = place_bodies(rng, sizes, box_lo=(-edge / 2, -edge / 2, 0.0),
-                            box_hi=(edge / 2, edge / 2, edge))
+    pos, vel = lattice_placement(rng, sizes)
     sc = _assemble(pos, vel, 1.0, friction=friction, dt=dt, iterations=iterations)
     steps = int(rng.integers(1, 101))
     return sc, steps

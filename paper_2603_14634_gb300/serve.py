@@ -1,0 +1,197 @@
+"""Continuous-batching server of PBD-R scene requests on one GPU.
+
+A request is a scene plus a number of substeps.  The server keeps every
+admitted scene resident on the device and runs in ticks; every tick it
+
+1. admits, first come first served, the requests that have arrived, as long
+   as the HBM ledger (an estimate of the device bytes per particle against
+   the budget) allows - requests arriving while others run join the next
+   tick, so their work shares the batched launches of the others;
+2. advances every resident request by one substep in ONE batched pbdr_step
+   call (a scene's result does not depend on which other scenes share the
+   call, so a request gets the same bytes alone or in the mix);
+3. retires the requests that have received all their substeps: reads back
+   their final state and destroys their scene, which frees their device
+   ranges for later requests.
+
+Latency of a request = completion time - arrival time (wall clock); the tick
+latency is the time of one batched substep of all resident requests.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+# device bytes held per resident particle (state, rest offsets, neighbour
+# lists, scratch and plan buffers), used by the admission ledger
+BYTES_PER_PARTICLE = 320
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    scene: object
+    steps: int
+    arrival: float
+    admitted: Optional[float] = None
+    done: Optional[float] = None
+    sid: Optional[int] = None
+    remaining: int = 0
+
+
+class Server:
+    """Continuous batching over a ``binding.Context``-like object.
+
+    ``ctx_factory`` builds the context (a fake one in host-only tests);
+    ``clock`` returns seconds (``time.perf_counter`` by default).
+    """
+
+    def __init__(self, hbm_budget_bytes: int = 120 << 30, device: int = 0,
+                 ctx_factory: Optional[Callable[[], object]] = None,
+                 clock: Callable[[], float] = time.perf_counter, stream=None,
+                 bytes_per_particle: int = BYTES_PER_PARTICLE):
+        if ctx_factory is None:
+            from .binding import Context, OPT_AUTOTUNE, OPT_GRAPHS
+
+            def ctx_factory():
+                c = Context(device, hbm_budget_bytes)
+                # the resident set changes every few ticks: plain launches, no tuning
+                c.set_option(OPT_GRAPHS, 0)
+                c.set_option(OPT_AUTOTUNE, 0)
+                return c
+        self.ctx = ctx_factory()
+        self.budget = hbm_budget_bytes
+        self.bpp = bytes_per_particle
+        self.clock = clock
+        self.stream = stream
+        self.pending: collections.deque = collections.deque()
+        self.active: Dict[int, Request] = {}
+        self.finished: List[Request] = []
+        self.results: Dict[int, tuple] = {}
+        self.ledger = 0
+        self.tick_ms: List[float] = []
+        self.host_ms = {"admit": 0.0, "step": 0.0, "retire": 0.0}
+        self.ticks = 0
+        self.work_done = 0            # particle-iterations
+        self._next = 0
+        self.t0 = None
+
+    # ---- requests ----------------------------------------------------------
+    def submit(self, scene, steps: int, arrival: float = 0.0) -> int:
+        """Queues a request (arrival in seconds from the start of run())."""
+        if steps < 1:
+            raise ValueError("a request needs at least one substep")
+        rid = self._next
+        self._next += 1
+        self.pending.append(Request(rid, scene, int(steps), float(arrival), remaining=int(steps)))
+        return rid
+
+    def _cost(self, req: Request) -> int:
+        return self.bpp * int(req.scene.num_particles)
+
+    def _admit(self, now: float) -> int:
+        n = 0
+        while self.pending and self.pending[0].arrival <= now:
+            req = self.pending[0]
+            cost = self._cost(req)
+            if self.active and self.ledger + cost > self.budget:
+                break                  # wait for memory to free up (FIFO: no overtaking)
+            try:
+                sid = self.ctx.create_scene(req.scene)
+            except RuntimeError as e:  # the library's own budget check
+                if getattr(e, "code", None) == -3 and self.active:
+                    break
+                raise
+            self.pending.popleft()
+            req.sid = sid
+            req.admitted = now
+            self.ledger += cost
+            self.active[req.rid] = req
+            n += 1
+        return n
+
+    def _retire(self, now: float):
+        done = [r for r in self.active.values() if r.remaining == 0]
+        for req in done:
+            pos, vel, err = self.ctx.read_state(req.sid, self.stream)
+            self.results[req.rid] = (pos, vel, err)
+            self.ctx.destroy_scene(req.sid)
+            self.ledger -= self._cost(req)
+            req.done = now
+            del self.active[req.rid]
+            self.finished.append(req)
+
+    # ---- main loop -----------------------------------------------------------
+    def tick(self) -> bool:
+        """One admission + batched substep + retirement round; False when idle."""
+        t_0 = self.clock()
+        now = t_0 - self.t0
+        self._admit(now)
+        if not self.active:
+            return bool(self.pending)
+        ids = [r.sid for r in self.active.values()]
+        t_a = self.clock()
+        self.ctx.step(ids, 1, self.stream)
+        for r in self.active.values():
+            r.remaining -= 1
+            self.work_done += int(r.scene.num_particles) * int(r.scene.iterations)
+        t_b = self.clock()
+        self._retire(t_b - self.t0)          # reads back finished ones (synchronises)
+        t_c = self.clock()
+        self.host_ms["admit"] += (t_a - t_0) * 1e3
+        self.host_ms["step"] += (t_b - t_a) * 1e3
+        self.host_ms["retire"] += (t_c - t_b) * 1e3
+        self.tick_ms.append((t_c - t_a) * 1e3)
+        self.ticks += 1
+        return True
+
+    def run(self, realtime: bool = True, max_ticks: Optional[int] = None) -> dict:
+        """Serves until every submitted request is finished.  With realtime
+        the arrival times are honoured against the wall clock (idle gaps are
+        slept through); otherwise every request counts as arrived."""
+        self.t0 = self.clock()
+        if not realtime:
+            for r in self.pending:
+                r.arrival = 0.0
+        while self.pending or self.active:
+            if max_ticks is not None and self.ticks >= max_ticks:
+                break
+            if not self.active and self.pending:
+                wait = self.pending[0].arrival - (self.clock() - self.t0)
+                if wait > 0:
+                    if realtime:
+                        time.sleep(min(wait, 0.05))
+                    continue
+            self.tick()
+        return self.stats()
+
+    def stats(self) -> dict:
+        lat = np.array([(r.done - r.arrival) * 1e3 for r in self.finished]) if self.finished else np.zeros(0)
+        tk = np.array(self.tick_ms) if self.tick_ms else np.zeros(0)
+        wall = (self.clock() - self.t0) if self.t0 is not None else 0.0
+
+        def pct(a, q):
+            return float(np.percentile(a, q)) if a.size else None
+        return {
+            "requests": len(self.finished), "ticks": self.ticks, "wall_s": wall,
+            "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
+            "tick_ms_p50": pct(tk, 50), "tick_ms_p99": pct(tk, 99),
+            "particle_iters": self.work_done,
+            "host_ms_per_tick": {k: v / max(self.ticks, 1) for k, v in self.host_ms.items()},
+            "achieved_particle_iters_per_s": self.work_done / wall if wall > 0 else None,
+        }
+
+
+def poisson_trace(rate_hz: float, duration_s: float, seed: int = 0) -> np.ndarray:
+    """Arrival times of a Poisson process of the given rate (seeded)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            return np.array(out)
+        out.append(t)
