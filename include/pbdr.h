@@ -29,7 +29,9 @@
  *     that return device results to host buffers synchronise that stream;
  *     pbdr_step is asynchronous.
  *   - A context is bound to one device and is not thread-safe: one thread
- *     drives a context at a time.
+ *     drives a context at a time.  Its device buffers are shared by all its
+ *     calls, which therefore run in stream order: a caller that switches
+ *     streams between calls synchronises the earlier stream first.
  *   - Units are SI; state is FP32.
  */
 #ifndef PBDR_H
@@ -96,7 +98,9 @@ int pbdr_ctx_create(int device, size_t hbm_budget_bytes, pbdr_ctx **out);
 int pbdr_ctx_destroy(pbdr_ctx *ctx);
 
 /* Copies a scene into device memory (synchronous) and returns its handle.
- * Computes M_b, c_b and the rest offsets in FP64 on the host.
+ * Computes M_b, c_b and the rest offsets in FP64 on the host.  Slots and
+ * table ranges of destroyed scenes are reused; a call that reuses one first
+ * waits for the device to finish the work already queued.
  * Errors: PBDR_ERR_INVALID (descriptor check failed: sizes, offsets, masses,
  * radius, dt, iterations, plane normal), PBDR_ERR_BUDGET, PBDR_ERR_OOM,
  * PBDR_ERR_UNSUPPORTED (flags). */

@@ -101,22 +101,28 @@ struct SceneHost {
   int32_t c0 = 0, nc = 0;          // chunk range
 };
 
+// A step plan: the host-side description of one batched substep over a list
+// of scenes.  Plans own no device memory: their small tables (hash bases,
+// segment tables, wrench and class lists) live in `tab` and are copied into
+// the context's table buffer, in stream order, when the plan becomes the
+// active one; the streaming form's sort and cell scratch is the context's.
 struct Plan {
   std::vector<int32_t> ids;
   int32_t np = 0, nb = 0;
   int32_t pbase = 0, bbase = 0;
   bool pcontig = true, bcontig = true;
-  DevBuf pmap, bmap, hbase;
   uint32_t T_total = 0;
   int key_bits = 0;
-  DevBuf keys_a, keys_b, vals_a, vals_b, hist, cstart, cend, spos;
   std::vector<int32_t> wrench_list;
-  DevBuf wlist;
   int kmax = 0;
   bool std_any = false;
   std::vector<int64_t> seg_off;    // per plan scene: first plan particle (n+1)
   std::vector<uint32_t> hbase_host;
   int sorted_in_b = 0;             // where the last sort left its result
+  // device tables (int32 words); offsets into tab, -1 = absent.  pseg/bseg:
+  // nseg + 1 segment starts (plan index) followed by nseg global bases
+  std::vector<int32_t> tab;
+  int32_t o_hbase = -1, o_wlist = -1, o_pseg = -1, o_bseg = -1, nseg = 0;
   // scene-resident form: size classes of scenes, each one persistent launch
   bool fused = false;
   struct FClass {
@@ -127,14 +133,24 @@ struct Plan {
     int grid = 0;
     int32_t n = 0;
     std::vector<int32_t> ids;
-    DevBuf list;
+    int32_t o_list = -1;           // offset of the scene list in tab
   };
   std::array<FClass, 4> classes;
-  Plan *rest = nullptr;            // scenes too large for a class (streaming form)
+  std::unique_ptr<Plan> rest;      // scenes too large for a class (streaming form)
   bool tuned = false;              // launch shapes picked by the autotuner
   cudaGraphExec_t graph = nullptr; // one substep, captured
+  uint64_t graph_gen = 0;          // context buffer generation the graph saw
   int64_t graph_launches = 0;
+  uint64_t last_use = 0;           // for least-recently-used eviction
+  Plan() = default;
+  Plan(const Plan &) = delete;
+  Plan &operator=(const Plan &) = delete;
+  ~Plan() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
 };
+
+constexpr size_t kMaxCachedPlans = 16;
 
 constexpr int kClassCaps[4] = {1024, 2048, 4096, 8192};
 constexpr int kClassThreads[4] = {256, 256, 512, 512};
@@ -173,6 +189,11 @@ struct pbdr_ctx {
   std::vector<BodyRec> bh;
   std::vector<BodyWrench> wh;
   std::map<std::vector<int32_t>, std::unique_ptr<Plan>> plans;
+  uint64_t use_clock = 0;
+  // tables of the active plan and the streaming form's scratch (grow-only)
+  DevBuf tab, s_keys_a, s_keys_b, s_vals_a, s_vals_b, s_hist, s_cstart, s_cend, s_spos, s_pmap, s_bmap;
+  const Plan *active = nullptr;
+  uint64_t gen = 1;                // bumped whenever a device buffer moves (graphs recapture)
   Plan *last_nbr_plan = nullptr;
   int64_t last_launches = 0;
   DevBuf stage_pos, stage_vel, seg_p0, seg_off, err_ids, err_out;
@@ -197,6 +218,7 @@ int dev_alloc(pbdr_ctx *c, DevBuf &b, size_t bytes) {
                                      " > " + std::to_string(c->budget) + " bytes)");
   b.release();
   c->used -= freed;
+  ++c->gen;
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     b.p = nullptr;
@@ -208,6 +230,7 @@ int dev_alloc(pbdr_ctx *c, DevBuf &b, size_t bytes) {
 }
 
 void dev_free(pbdr_ctx *c, DevBuf &b) {
+  if (b.p) ++c->gen;
   c->used -= b.bytes;
   b.release();
 }
@@ -217,6 +240,8 @@ int dev_grow(pbdr_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
   if (b.bytes >= bytes) return PBDR_OK;
   if (c->budget && c->used + bytes > c->budget)
     return fail(PBDR_ERR_BUDGET, "device memory budget exceeded");
+  // kernels in flight on any stream may still use the old buffer
+  if (b.p) CUDA_TRY(cudaDeviceSynchronize());
   void *np = nullptr;
   cudaError_t e = cudaMalloc(&np, bytes);
   if (e != cudaSuccess) return fail(PBDR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -294,17 +319,9 @@ int check_scene(pbdr_ctx *c, pbdr_scene s) {
   return PBDR_OK;
 }
 
-int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out, int streaming_only = 0);
-
-// scene-resident plan: scenes grouped by size class, the rest streamed
-int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) {
-  std::vector<int32_t> key(ids, ids + n);
-  key.insert(key.begin(), -2);
-  auto it = c->plans.find(key);
-  if (it != c->plans.end()) {
-    *out = it->second.get();
-    return PBDR_OK;
-  }
+// Validates ids (alive, no duplicates).
+int check_ids(pbdr_ctx *c, const pbdr_scene *ids, int32_t n) {
+  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
   std::vector<char> seen(c->sh.size(), 0);
   for (int32_t i = 0; i < n; ++i) {
     int rc = check_scene(c, ids[i]);
@@ -312,23 +329,91 @@ int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) 
     if (seen[ids[i]]) return fail(PBDR_ERR_INVALID, "duplicate scene id " + std::to_string(ids[i]));
     seen[ids[i]] = 1;
   }
-  auto P = std::make_unique<Plan>();
-  P->ids.assign(ids, ids + n);
-  P->fused = true;
+  return PBDR_OK;
+}
+
+// streaming-form plan of ids[0..n); its tables are appended to `tab` (the
+// plan's own, or the parent scene-resident plan's)
+int fill_stream_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P, std::vector<int32_t> &tab) {
+  P.ids.assign(ids, ids + n);
+  P.hbase_host.assign(std::max<size_t>(c->sh.size(), 1), 0u);
+  P.seg_off.assign(1, 0);
+  std::vector<int32_t> pstart(1, 0), pb0, bstart(1, 0), bb0;
+  uint64_t tsum = 0;
+  int32_t next_p = -1, next_b = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    const SceneHost &S = c->sh[ids[i]];
+    if (i == 0) {
+      P.pbase = S.p0;
+      P.bbase = S.b0;
+    } else {
+      if (S.p0 != next_p) P.pcontig = false;
+      if (S.b0 != next_b) P.bcontig = false;
+    }
+    next_p = S.p0 + S.np;
+    next_b = S.b0 + S.nb;
+    P.hbase_host[ids[i]] = (uint32_t)tsum;
+    tsum += S.par.T;
+    if (tsum > 0xF0000000ull) return fail(PBDR_ERR_INVALID, "hash tables of one step exceed 2^32 buckets");
+    P.np += S.np;
+    P.nb += S.nb;
+    P.seg_off.push_back(P.np);
+    pstart.push_back(P.np);
+    pb0.push_back(S.p0);
+    bstart.push_back(P.nb);
+    bb0.push_back(S.b0);
+    P.kmax = std::max(P.kmax, S.par.iterations);
+    P.std_any |= (S.par.flags & kStdVelocity) != 0;
+    if (S.wrench_bodies)
+      for (int32_t b = S.b0; b < S.b0 + S.nb; ++b)
+        if (c->bh[b].has_wrench) P.wrench_list.push_back(b);
+  }
+  P.T_total = (uint32_t)tsum;
+  int bits = 1;
+  while (bits < 32 && (1ull << bits) < tsum) ++bits;
+  P.key_bits = bits;
+  P.nseg = n;
+  P.o_hbase = (int32_t)tab.size();
+  for (uint32_t h : P.hbase_host) tab.push_back((int32_t)h);
+  if (!P.pcontig) {
+    P.o_pseg = (int32_t)tab.size();
+    tab.insert(tab.end(), pstart.begin(), pstart.end());
+    tab.insert(tab.end(), pb0.begin(), pb0.end());
+  }
+  if (!P.bcontig) {
+    P.o_bseg = (int32_t)tab.size();
+    tab.insert(tab.end(), bstart.begin(), bstart.end());
+    tab.insert(tab.end(), bb0.begin(), bb0.end());
+  }
+  if (!P.wrench_list.empty()) {
+    P.o_wlist = (int32_t)tab.size();
+    tab.insert(tab.end(), P.wrench_list.begin(), P.wrench_list.end());
+  }
+  int rc;
+  if (P.std_any && !c->Xinit.p) {
+    if ((rc = dev_alloc(c, c->Xinit, (size_t)c->pcap * sizeof(float4)))) return rc;
+  }
+  return PBDR_OK;
+}
+
+// scene-resident plan: scenes grouped by size class, the rest streamed
+int fill_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P) {
+  P.ids.assign(ids, ids + n);
+  P.fused = true;
   std::vector<int32_t> rest;
   for (int32_t i = 0; i < n; ++i) {
     const SceneHost &S = c->sh[ids[i]];
     int k = 0;
     while (k < 4 && S.np > kClassCaps[k]) ++k;
     if (k < 4)
-      P->classes[k].ids.push_back(ids[i]);
+      P.classes[k].ids.push_back(ids[i]);
     else
       rest.push_back(ids[i]);
   }
   if (!c->num_sms) CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   int rc;
   for (int k = 0; k < 4; ++k) {
-    Plan::FClass &F = P->classes[k];
+    Plan::FClass &F = P.classes[k];
     F.ncap = kClassCaps[k];
     F.dx_shared = fused_layout(F.ncap, true, false, true).bytes <= 220 * 1024;
     F.v_shared = F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024;
@@ -338,8 +423,8 @@ int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) 
     // largest scenes first: the persistent CTAs then finish together
     std::stable_sort(F.ids.begin(), F.ids.end(),
                      [&](int32_t a, int32_t b) { return c->sh[a].np > c->sh[b].np; });
-    if ((rc = dev_alloc(c, F.list, F.ids.size() * 4))) return rc;
-    CUDA_TRY(cudaMemcpy(F.list.p, F.ids.data(), F.ids.size() * 4, cudaMemcpyHostToDevice));
+    F.o_list = (int32_t)P.tab.size();
+    P.tab.insert(P.tab.end(), F.ids.begin(), F.ids.end());
     const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.v_shared, F.threads);
     if (per_sm < 1) return fail(PBDR_ERR_CUDA, "scene-resident kernel does not fit on an SM");
     F.grid = std::min<int>(F.n, per_sm * c->num_sms);
@@ -348,113 +433,100 @@ int build_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out) 
     }
   }
   if (!c->tickets.p && (rc = dev_alloc(c, c->tickets, 64))) return rc;
+  if (!rest.empty()) {
+    P.rest = std::make_unique<Plan>();
+    if ((rc = fill_stream_plan(c, rest.data(), (int32_t)rest.size(), *P.rest, P.tab))) return rc;
+  }
+  return PBDR_OK;
+}
+
+void erase_plan(pbdr_ctx *c, std::map<std::vector<int32_t>, std::unique_ptr<Plan>>::iterator it) {
+  Plan *P = it->second.get();
+  if (c->active == P) c->active = nullptr;
+  if (c->last_fused_plan == P) c->last_fused_plan = nullptr;
+  if (c->last_nbr_plan == P || (P->rest && c->last_nbr_plan == P->rest.get())) c->last_nbr_plan = nullptr;
+  c->plans.erase(it);
+}
+
+// the plan for ids[0..n) (key prefix -2: scene-resident where scenes fit,
+// -1: streaming form only), cached; least recently used plans are evicted
+int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out, int streaming_only = 0) {
+  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
+  const bool fused = !streaming_only && c->path == 0;
+  std::vector<int32_t> key(ids, ids + n);
+  key.insert(key.begin(), fused ? -2 : -1);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    it->second->last_use = ++c->use_clock;
+    *out = it->second.get();
+    return PBDR_OK;
+  }
+  int rc = check_ids(c, ids, n);
+  if (rc) return rc;
+  auto P = std::make_unique<Plan>();
+  rc = fused ? fill_fused_plan(c, ids, n, *P) : fill_stream_plan(c, ids, n, *P, P->tab);
+  if (rc) return rc;
+  P->last_use = ++c->use_clock;
   Plan *raw = P.get();
   c->plans[key] = std::move(P);
-  if (!rest.empty()) {
-    if ((rc = build_plan(c, rest.data(), (int32_t)rest.size(), &raw->rest, 1))) return rc;
+  while (c->plans.size() > kMaxCachedPlans) {
+    auto lru = c->plans.end();
+    for (auto i = c->plans.begin(); i != c->plans.end(); ++i)
+      if (i->second.get() != raw && (lru == c->plans.end() || i->second->last_use < lru->second->last_use)) lru = i;
+    if (lru == c->plans.end()) break;
+    erase_plan(c, lru);
   }
   *out = raw;
   return PBDR_OK;
 }
 
-int build_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan **out, int streaming_only) {
-  if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
-  if (!streaming_only && c->path == 0) return build_fused_plan(c, ids, n, out);
-  std::vector<int32_t> key(ids, ids + n);
-  key.insert(key.begin(), -1);
-  auto it = c->plans.find(key);
-  if (it != c->plans.end()) {
-    *out = it->second.get();
-    return PBDR_OK;
-  }
-  std::vector<char> seen(c->sh.size(), 0);
-  for (int32_t i = 0; i < n; ++i) {
-    int rc = check_scene(c, ids[i]);
-    if (rc) return rc;
-    if (seen[ids[i]]) return fail(PBDR_ERR_INVALID, "duplicate scene id " + std::to_string(ids[i]));
-    seen[ids[i]] = 1;
-  }
-  auto P = std::make_unique<Plan>();
-  P->ids.assign(ids, ids + n);
-  std::vector<int32_t> pmap, bmap;
-  P->hbase_host.assign(std::max<size_t>(c->sh.size(), 1), 0u);
-  P->seg_off.push_back(0);
-  uint64_t tsum = 0;
-  int32_t next_p = -1, next_b = -1;
-  for (int32_t i = 0; i < n; ++i) {
-    const SceneHost &S = c->sh[ids[i]];
-    if (i == 0) {
-      P->pbase = S.p0;
-      P->bbase = S.b0;
-    } else {
-      if (S.p0 != next_p) P->pcontig = false;
-      if (S.b0 != next_b) P->bcontig = false;
-    }
-    next_p = S.p0 + S.np;
-    next_b = S.b0 + S.nb;
-    for (int32_t k = 0; k < S.np; ++k) pmap.push_back(S.p0 + k);
-    for (int32_t k = 0; k < S.nb; ++k) bmap.push_back(S.b0 + k);
-    P->hbase_host[ids[i]] = (uint32_t)tsum;
-    tsum += S.par.T;
-    if (tsum > 0xF0000000ull) return fail(PBDR_ERR_INVALID, "hash tables of one step exceed 2^32 buckets");
-    P->np += S.np;
-    P->nb += S.nb;
-    P->seg_off.push_back(P->np);
-    P->kmax = std::max(P->kmax, S.par.iterations);
-    P->std_any |= (S.par.flags & kStdVelocity) != 0;
-    if (S.wrench_bodies)
-      for (int32_t b = S.b0; b < S.b0 + S.nb; ++b)
-        if (c->bh[b].has_wrench) P->wrench_list.push_back(b);
-  }
-  P->T_total = (uint32_t)tsum;
-  int bits = 1;
-  while (bits < 32 && (1ull << bits) < tsum) ++bits;
-  P->key_bits = bits;
-  int rc;
-  if (!P->pcontig) {
-    if ((rc = dev_alloc(c, P->pmap, pmap.size() * 4))) return rc;
-    CUDA_TRY(cudaMemcpy(P->pmap.p, pmap.data(), pmap.size() * 4, cudaMemcpyHostToDevice));
-  }
-  if (!P->bcontig) {
-    if ((rc = dev_alloc(c, P->bmap, bmap.size() * 4))) return rc;
-    CUDA_TRY(cudaMemcpy(P->bmap.p, bmap.data(), bmap.size() * 4, cudaMemcpyHostToDevice));
-  }
-  if ((rc = dev_alloc(c, P->hbase, P->hbase_host.size() * 4))) return rc;
-  CUDA_TRY(cudaMemcpy(P->hbase.p, P->hbase_host.data(), P->hbase_host.size() * 4, cudaMemcpyHostToDevice));
-  const size_t npb = (size_t)std::max(P->np, 1);
-  if ((rc = dev_alloc(c, P->keys_a, npb * 4))) return rc;
-  if ((rc = dev_alloc(c, P->keys_b, npb * 4))) return rc;
-  if ((rc = dev_alloc(c, P->vals_a, npb * 4))) return rc;
-  if ((rc = dev_alloc(c, P->vals_b, npb * 4))) return rc;
-  if ((rc = dev_alloc(c, P->spos, npb * sizeof(float4)))) return rc;
-  if ((rc = dev_alloc(c, P->hist, radix_hist_words(P->np) * 4))) return rc;
-  if ((rc = dev_alloc(c, P->cstart, (size_t)std::max<uint32_t>(P->T_total, 1) * 4))) return rc;
-  if ((rc = dev_alloc(c, P->cend, (size_t)std::max<uint32_t>(P->T_total, 1) * 4))) return rc;
-  if (!P->wrench_list.empty()) {
-    if ((rc = dev_alloc(c, P->wlist, P->wrench_list.size() * 4))) return rc;
-    CUDA_TRY(cudaMemcpy(P->wlist.p, P->wrench_list.data(), P->wrench_list.size() * 4, cudaMemcpyHostToDevice));
-  }
-  if (P->std_any && !c->Xinit.p) {
-    if ((rc = dev_alloc(c, c->Xinit, (size_t)c->pcap * sizeof(float4)))) return rc;
-  }
-  *out = P.get();
-  c->plans[key] = std::move(P);
-  return PBDR_OK;
-}
-
 void invalidate_plans(pbdr_ctx *c) {
-  for (auto &kv : c->plans) {
-    Plan &P = *kv.second;
-    for (DevBuf *b : {&P.pmap, &P.bmap, &P.hbase, &P.keys_a, &P.keys_b, &P.vals_a, &P.vals_b,
-                      &P.hist, &P.cstart, &P.cend, &P.spos, &P.wlist})
-      dev_free(c, *b);
-    for (auto &F : P.classes) dev_free(c, F.list);
-    if (P.graph) cudaGraphExecDestroy(P.graph);
-    P.graph = nullptr;
-  }
-  c->plans.clear();
+  while (!c->plans.empty()) erase_plan(c, c->plans.begin());
   c->last_nbr_plan = nullptr;
   c->last_fused_plan = nullptr;
+}
+
+// drops the cached plans that contain scene s
+void drop_plans_with(pbdr_ctx *c, pbdr_scene s) {
+  for (auto it = c->plans.begin(); it != c->plans.end();) {
+    auto nx = std::next(it);
+    if (std::find(it->first.begin() + 1, it->first.end(), s) != it->first.end()) erase_plan(c, it);
+    it = nx;
+  }
+}
+
+// Makes P the active plan on stream s: sizes the streaming scratch, copies
+// the plan's tables into the context's table buffer and expands the particle
+// and body maps of non-contiguous scene lists.  Stream-ordered after every
+// earlier use of those buffers on s.
+int activate(pbdr_ctx *c, Plan *P, cudaStream_t s) {
+  if (c->active == P) return PBDR_OK;
+  Plan *S = P->fused ? P->rest.get() : P;
+  int rc;
+  if (S && S->np > 0) {
+    const size_t npb = (size_t)S->np;
+    if ((rc = dev_alloc(c, c->s_keys_a, npb * 4)) || (rc = dev_alloc(c, c->s_keys_b, npb * 4)) ||
+        (rc = dev_alloc(c, c->s_vals_a, npb * 4)) || (rc = dev_alloc(c, c->s_vals_b, npb * 4)) ||
+        (rc = dev_alloc(c, c->s_spos, npb * sizeof(float4))) ||
+        (rc = dev_alloc(c, c->s_hist, radix_hist_words(S->np) * 4)) ||
+        (rc = dev_alloc(c, c->s_cstart, (size_t)std::max<uint32_t>(S->T_total, 1) * 4)) ||
+        (rc = dev_alloc(c, c->s_cend, (size_t)std::max<uint32_t>(S->T_total, 1) * 4)))
+      return rc;
+    if (!S->pcontig && (rc = dev_alloc(c, c->s_pmap, npb * 4))) return rc;
+    if (!S->bcontig && (rc = dev_alloc(c, c->s_bmap, (size_t)std::max(S->nb, 1) * 4))) return rc;
+  }
+  if (!P->tab.empty()) {
+    if ((rc = dev_alloc(c, c->tab, P->tab.size() * 4))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(c->tab.p, P->tab.data(), P->tab.size() * 4, cudaMemcpyHostToDevice, s));
+  }
+  if (S && S->np > 0) {
+    const int32_t *t = c->tab.as<int32_t>();
+    if (!S->pcontig) launch_expand_map(t + S->o_pseg, t + S->o_pseg + S->nseg + 1, S->nseg, c->s_pmap.as<int32_t>(), s);
+    if (!S->bcontig) launch_expand_map(t + S->o_bseg, t + S->o_bseg + S->nseg + 1, S->nseg, c->s_bmap.as<int32_t>(), s);
+    CUDA_TRY(cudaGetLastError());
+  }
+  c->active = P;
+  return PBDR_OK;
 }
 
 // event of the profiling pool, recorded on s (returns its pool index)
@@ -491,22 +563,22 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   int in_b = 0;
   {
   StageTimer tm(c, s, 2, launches);
-  launches += radix_sort_pairs(P.keys_a.as<uint32_t>(), P.vals_a.as<uint32_t>(), P.keys_b.as<uint32_t>(),
-                               P.vals_b.as<uint32_t>(), P.hist.as<uint32_t>(), P.np, P.key_bits, &in_b, s);
+  launches += radix_sort_pairs(c->s_keys_a.as<uint32_t>(), c->s_vals_a.as<uint32_t>(), c->s_keys_b.as<uint32_t>(),
+                               c->s_vals_b.as<uint32_t>(), c->s_hist.as<uint32_t>(), P.np, P.key_bits, &in_b, s);
   }
   P.sorted_in_b = in_b;
   StageTimer tm(c, s, 3, launches);
-  CUDA_TRY(cudaMemsetAsync(P.cstart.p, 0xFF, (size_t)std::max<uint32_t>(P.T_total, 1) * 4, s));
-  const uint32_t *sk = in_b ? P.keys_b.as<uint32_t>() : P.keys_a.as<uint32_t>();
-  const uint32_t *sv = in_b ? P.vals_b.as<uint32_t>() : P.vals_a.as<uint32_t>();
+  CUDA_TRY(cudaMemsetAsync(c->s_cstart.p, 0xFF, (size_t)std::max<uint32_t>(P.T_total, 1) * 4, s));
+  const uint32_t *sk = in_b ? c->s_keys_b.as<uint32_t>() : c->s_keys_a.as<uint32_t>();
+  const uint32_t *sv = in_b ? c->s_vals_b.as<uint32_t>() : c->s_vals_a.as<uint32_t>();
   CellArgs ca{};
   ca.skeys = sk;
   ca.svals = sv;
   ca.Xp = Xp;
   ca.pbody = c->pbody.as<int32_t>();
-  ca.cstart = P.cstart.as<uint32_t>();
-  ca.cend = P.cend.as<uint32_t>();
-  ca.spos = P.spos.as<float4>();
+  ca.cstart = c->s_cstart.as<uint32_t>();
+  ca.cend = c->s_cend.as<uint32_t>();
+  ca.spos = c->s_spos.as<float4>();
   ca.np = P.np;
   launches += launch_cells(ca, s);
   NbrArgs na{};
@@ -514,14 +586,14 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   na.svals = sv;
   na.Xp = Xp;
   na.pbody = c->pbody.as<int32_t>();
-  na.pmap = P.pcontig ? nullptr : P.pmap.as<int32_t>();
+  na.pmap = P.pcontig ? nullptr : c->s_pmap.as<int32_t>();
   na.pbase = P.pbase;
-  na.spos = P.spos.as<float4>();
-  na.cstart = P.cstart.as<uint32_t>();
-  na.cend = P.cend.as<uint32_t>();
+  na.spos = c->s_spos.as<float4>();
+  na.cstart = c->s_cstart.as<uint32_t>();
+  na.cend = c->s_cend.as<uint32_t>();
   na.bodies = c->bodies.as<BodyRec>();
   na.scenes = c->scenes.as<ScenePar>();
-  na.hbase = P.hbase.as<uint32_t>();
+  na.hbase = reinterpret_cast<const uint32_t *>(c->tab.as<int32_t>() + P.o_hbase);
   na.nbr_cnt = c->nbr_cnt.as<int32_t>();
   na.nbr = c->nbr.as<int32_t>();
   na.nbr_stride = c->pcap;
@@ -545,12 +617,12 @@ PredictArgs predict_args(pbdr_ctx *c, Plan &P, const float4 *X0, const float4 *V
   a.bodies = c->bodies.as<BodyRec>();
   a.scenes = c->scenes.as<ScenePar>();
   a.wrench = c->wrench.as<BodyWrench>();
-  a.pmap = P.pcontig ? nullptr : P.pmap.as<int32_t>();
+  a.pmap = P.pcontig ? nullptr : c->s_pmap.as<int32_t>();
   a.pbase = P.pbase;
   a.np = P.np;
-  a.hbase = P.hbase.as<uint32_t>();
-  a.keys = P.keys_a.as<uint32_t>();
-  a.vals = P.vals_a.as<uint32_t>();
+  a.hbase = reinterpret_cast<const uint32_t *>(c->tab.as<int32_t>() + P.o_hbase);
+  a.keys = c->s_keys_a.as<uint32_t>();
+  a.vals = c->s_vals_a.as<uint32_t>();
   a.predict = predict;
   return a;
 }
@@ -580,7 +652,7 @@ int launch_class(pbdr_ctx *c, Plan &P, int k, cudaStream_t st) {
   a.nbr_stride = c->pcap;
   a.nbr_cap = std::min(c->nbr_cap, kFusedNbrCap);
   a.scene_err = c->scene_err.as<uint32_t>();
-  a.scene_list = F.list.as<int32_t>();
+  a.scene_list = c->tab.as<int32_t>() + F.o_list;
   a.nscenes = F.n;
   a.ticket = c->tickets.as<uint32_t>() + k;
   a.ncap = F.ncap;
@@ -769,7 +841,7 @@ int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
     wa.Q = c->Q.as<float4>();
     wa.bodies = c->bodies.as<BodyRec>();
     wa.wrench = c->wrench.as<BodyWrench>();
-    wa.blist = P.wlist.as<int32_t>();
+    wa.blist = c->tab.as<int32_t>() + P.o_wlist;
     wa.nb = (int32_t)P.wrench_list.size();
     launches += launch_wrench(wa, s);
   }
@@ -794,7 +866,7 @@ int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   ia.scenes = c->scenes.as<ScenePar>();
   ia.quat = c->quat.as<float4>();
   ia.bcom = c->bcom.as<float4>();
-  ia.bmap = P.bcontig ? nullptr : P.bmap.as<int32_t>();
+  ia.bmap = P.bcontig ? nullptr : c->s_bmap.as<int32_t>();
   ia.bbase = P.bbase;
   ia.nbodies = P.nb;
   ia.scene_err = c->scene_err.as<uint32_t>();
@@ -955,7 +1027,6 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
       sid = i;
       break;
     }
-  const int32_t old_pcap = c->pcap;
   // work chunks of the scene-resident kernel: up to kChunk particles of one body
   int32_t nchunks = 0;
   for (int32_t b = 0; b < B; ++b) nchunks += (d->body_off[b + 1] - d->body_off[b] + kChunk - 1) / kChunk;
@@ -986,7 +1057,6 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     give_back();
     return rc;
   }
-  if (c->pcap != old_pcap) invalidate_plans(c);
 
   // host-side FP64 rest shape (Mueller et al. 2005): M, c0, q = x0 - c0
   std::vector<float4> X(N), V(N), Q(N);
@@ -1077,6 +1147,8 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   std::vector<float4> quat(B, make_float4(0.f, 0.f, 0.f, 1.f));
   std::vector<BodyWrench> wr(B);
   std::memset(wr.data(), 0, sizeof(BodyWrench) * (size_t)B);
+  // a reused scene slot or table range may still be in use by steps in flight
+  if (!p_top || !b_top || !c_top || sid < (int32_t)c->sh.size()) CUDA_TRY(cudaDeviceSynchronize());
   if (N > 0) {
     CUDA_TRY(cudaMemcpy(c->X[0].as<float4>() + S.p0, X.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->V[0].as<float4>() + S.p0, V.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
@@ -1115,8 +1187,6 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   c->np_used = c->pa.top;
   c->nb_used = c->ba.top;
   c->nc_used = c->ca.top;
-  // plans hold per-scene tables sized by the scene count
-  invalidate_plans(c);
   *out = sid;
   return PBDR_OK;
 }
@@ -1130,7 +1200,7 @@ int pbdr_destroy_scene(pbdr_ctx *c, pbdr_scene s) {
   c->pa.give(S.p0, S.np);
   c->ba.give(S.b0, S.nb);
   c->ca.give(S.c0, S.nc);
-  invalidate_plans(c);
+  drop_plans_with(c, s);
   return PBDR_OK;
 }
 
@@ -1141,6 +1211,7 @@ int pbdr_set_body_wrench(pbdr_ctx *c, pbdr_scene s, int32_t body, const float F[
   SceneHost &S = c->sh[s];
   if (body < 0 || body >= S.nb) return fail(PBDR_ERR_INVALID, "body index out of range");
   if (!F || !tau || !finite3(F) || !finite3(tau)) return fail(PBDR_ERR_INVALID, "force and torque must be finite");
+  CUDA_TRY(cudaDeviceSynchronize());   // steps in flight keep the old wrench
   const int32_t gb = S.b0 + body;
   const bool on = F[0] != 0.f || F[1] != 0.f || F[2] != 0.f || tau[0] != 0.f || tau[1] != 0.f || tau[2] != 0.f;
   BodyWrench &w = c->wh[gb];
@@ -1156,7 +1227,7 @@ int pbdr_set_body_wrench(pbdr_ctx *c, pbdr_scene s, int32_t body, const float F[
   else
     S.par.flags &= ~kSceneHasWrench;
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + s, &S.par, sizeof(ScenePar), cudaMemcpyHostToDevice));
-  if (was != c->bh[gb].has_wrench) invalidate_plans(c);
+  if (was != c->bh[gb].has_wrench) drop_plans_with(c, s);
   return PBDR_OK;
 }
 
@@ -1168,22 +1239,28 @@ int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, v
   int rc = build_plan(c, ids, n, &P);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = activate(c, P, s))) return rc;
   int64_t launches = 0;
   if (substeps > 0 && P->fused && c->autotune && !P->tuned) {
     rc = autotune_fused(c, *P, s);
     if (rc) return rc;
   }
   const bool graphs = c->use_graphs && !c->profiling && s != nullptr && substeps > 0;
+  if (graphs && P->graph && P->graph_gen != c->gen) {   // a buffer it uses has moved
+    cudaGraphExecDestroy(P->graph);
+    P->graph = nullptr;
+  }
   if (graphs && !P->graph) {
     rc = capture_plan(c, *P, s);
     if (rc) return rc;
+    P->graph_gen = c->gen;
   }
   for (int32_t k = 0; k < substeps; ++k) {
     if (graphs) {
       CUDA_TRY(cudaGraphLaunch(P->graph, s));
       launches += P->graph_launches;
       if (P->fused) c->last_fused_plan = P;
-      if (!P->fused || P->rest) c->last_nbr_plan = P->fused ? P->rest : P;
+      if (!P->fused || P->rest) c->last_nbr_plan = P->fused ? P->rest.get() : P;
     } else {
       rc = substep(c, *P, s, launches);
       if (rc) return rc;
@@ -1244,6 +1321,7 @@ int pbdr_build_neighbors(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, void *st
   if (rc) return rc;
   if (P->np == 0) return PBDR_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = activate(c, P, s))) return rc;
   int64_t launches = 0;
   float4 *X0 = c->X[0].as<float4>();
   launches += launch_predict(predict_args(c, *P, X0, c->V[0].as<float4>(), X0, c->V[0].as<float4>(), 0), s);
@@ -1282,8 +1360,8 @@ int pbdr_read_neighbors(pbdr_ctx *c, pbdr_scene s, uint32_t *sorted_key, uint32_
   std::vector<uint32_t> k(N), v(N);
   if (N > 0 && !fused) {
     const int64_t so = P->seg_off[pos_in_plan];
-    const uint32_t *sk = P->sorted_in_b ? P->keys_b.as<uint32_t>() : P->keys_a.as<uint32_t>();
-    const uint32_t *sv = P->sorted_in_b ? P->vals_b.as<uint32_t>() : P->vals_a.as<uint32_t>();
+    const uint32_t *sk = P->sorted_in_b ? c->s_keys_b.as<uint32_t>() : c->s_keys_a.as<uint32_t>();
+    const uint32_t *sv = P->sorted_in_b ? c->s_vals_b.as<uint32_t>() : c->s_vals_a.as<uint32_t>();
     CUDA_TRY(cudaMemcpy(k.data(), sk + so, (size_t)N * 4, cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemcpy(v.data(), sv + so, (size_t)N * 4, cudaMemcpyDeviceToHost));
   }

@@ -193,6 +193,8 @@ int launch_neighbors(const NbrArgs &a, cudaStream_t s);
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_wrench(const WrenchArgs &a, cudaStream_t s);
 int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
+int launch_expand_map(const int32_t *seg_start, const int32_t *seg_base, int32_t nseg, int32_t *map,
+                      cudaStream_t s);
 int launch_scene_substep(const FusedArgs &a, int threads, cudaStream_t s);
 FusedLayout fused_layout(int ncap, bool dx_shared, bool v_shared, bool part_shared);
 int fused_max_blocks_per_sm(int ncap, bool dx_shared, bool v_shared, int threads);

@@ -453,9 +453,24 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a, int unpack) {
   }
 }
 
+// plan index -> global index over segments: map[seg_start[s] + j] = seg_base[s] + j
+__global__ void __launch_bounds__(256) k_expand_map(const int32_t *seg_start, const int32_t *seg_base,
+                                                    int32_t *map) {
+  const int sg = blockIdx.x;
+  const int32_t a = seg_start[sg], n = seg_start[sg + 1] - a, base = seg_base[sg];
+  for (int32_t j = threadIdx.x; j < n; j += blockDim.x) map[a + j] = base + j;
+}
+
 inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+int launch_expand_map(const int32_t *seg_start, const int32_t *seg_base, int32_t nseg, int32_t *map,
+                      cudaStream_t s) {
+  if (nseg <= 0) return 0;
+  k_expand_map<<<nseg, 256, 0, s>>>(seg_start, seg_base, map);
+  return 1;
+}
 
 int launch_predict(const PredictArgs &a, cudaStream_t s) {
   if (a.np <= 0) return 0;

@@ -3,16 +3,17 @@
 A request is a scene plus a number of substeps.  The server keeps every
 admitted scene resident on the device and runs in ticks; every tick it
 
-1. admits, first come first served, the requests that have arrived, as long
-   as the HBM ledger (an estimate of the device bytes per particle against
-   the budget) allows - requests arriving while others run join the next
-   tick, so their work shares the batched launches of the others;
-2. advances every resident request by one substep in ONE batched pbdr_step
-   call (a scene's result does not depend on which other scenes share the
-   call, so a request gets the same bytes alone or in the mix);
+1. advances every resident request by one substep in ONE batched pbdr_step
+   call, which returns at once (a scene's result does not depend on which
+   other scenes share the call, so a request gets the same bytes alone or
+   in the mix);
+2. while that substep runs on the GPU, admits, first come first served, the
+   requests that have arrived, as long as the HBM ledger (an estimate of the
+   device bytes per particle against the budget) allows - they join the
+   batch from the next tick on;
 3. retires the requests that have received all their substeps: reads back
-   their final state and destroys their scene, which frees their device
-   ranges for later requests.
+   their final states in one call and destroys their scenes, which frees
+   their device ranges for later requests.
 
 Latency of a request = completion time - arrival time (wall clock); the tick
 latency is the time of one batched substep of all resident requests.
@@ -116,9 +117,14 @@ class Server:
 
     def _retire(self, now: float):
         done = [r for r in self.active.values() if r.remaining == 0]
-        for req in done:
-            pos, vel, err = self.ctx.read_state(req.sid, self.stream)
-            self.results[req.rid] = (pos, vel, err)
+        if not done:
+            return
+        pos, vel, err = self.ctx.read_states([r.sid for r in done], stream=self.stream)
+        at = 0
+        for k, req in enumerate(done):
+            n = int(req.scene.num_particles)
+            self.results[req.rid] = (pos[at:at + n], vel[at:at + n], int(err[k]))
+            at += n
             self.ctx.destroy_scene(req.sid)
             self.ledger -= self._cost(req)
             req.done = now
@@ -127,25 +133,26 @@ class Server:
 
     # ---- main loop -----------------------------------------------------------
     def tick(self) -> bool:
-        """One admission + batched substep + retirement round; False when idle."""
+        """One batched substep + admission + retirement round; False when idle."""
         t_0 = self.clock()
-        now = t_0 - self.t0
-        self._admit(now)
-        if not self.active:
-            return bool(self.pending)
-        ids = [r.sid for r in self.active.values()]
+        stepped = bool(self.active)
+        if stepped:
+            ids = [r.sid for r in self.active.values()]
+            self.ctx.step(ids, 1, self.stream)      # asynchronous
+            for r in self.active.values():
+                r.remaining -= 1
+                self.work_done += int(r.scene.num_particles) * int(r.scene.iterations)
         t_a = self.clock()
-        self.ctx.step(ids, 1, self.stream)
-        for r in self.active.values():
-            r.remaining -= 1
-            self.work_done += int(r.scene.num_particles) * int(r.scene.iterations)
+        self._admit(t_a - self.t0)                 # host work overlaps the substep
         t_b = self.clock()
-        self._retire(t_b - self.t0)          # reads back finished ones (synchronises)
+        self._retire(t_b - self.t0)                # reads back finished ones (synchronises)
         t_c = self.clock()
-        self.host_ms["admit"] += (t_a - t_0) * 1e3
-        self.host_ms["step"] += (t_b - t_a) * 1e3
+        if not stepped:
+            return bool(self.pending or self.active)
+        self.host_ms["step"] += (t_a - t_0) * 1e3
+        self.host_ms["admit"] += (t_b - t_a) * 1e3
         self.host_ms["retire"] += (t_c - t_b) * 1e3
-        self.tick_ms.append((t_c - t_a) * 1e3)
+        self.tick_ms.append((t_c - t_0) * 1e3)
         self.ticks += 1
         return True
 

@@ -1,0 +1,87 @@
+"""Step plans are cached per scene list, hold no device memory of their own
+and are evicted least recently used; scene slots and table ranges of
+destroyed scenes are reused.  None of that may change a result: every scene
+must end bit-identical to the same scene stepped alone in a fresh context."""
+import numpy as np
+import pytest
+
+from paper_2603_14634_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(pbdr_lib, sc, steps, streaming):
+    with pbdr_lib.Context(0) as c:
+        c.set_path(streaming)
+        sid = c.create_scene(sc)
+        c.step(sid, steps)
+        return c.read_state(sid)
+
+
+@pytest.mark.parametrize("streaming", [False, True])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_rotating_subsets_past_the_plan_cache(pbdr_lib, streaming, graphs):
+    """24 distinct scene subsets (more than the cache keeps) stepped in
+    rotation, twice over, with graph replay on a side stream or plain
+    launches; the big scene (9375 particles) takes the streaming kernels."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    scs = [scenes.batch_scene(rng) for _ in range(9)]
+    scs.append(scenes.random_bodies_scene(seed=4, num_bodies=75))
+    steps = np.zeros(len(scs), int)
+    with pbdr_lib.Context(0) as c:
+        c.set_path(streaming)
+        c.set_option(pbdr_lib.OPT_GRAPHS, graphs)
+        c.set_option(pbdr_lib.OPT_AUTOTUNE, 0)
+        ids = [c.create_scene(s) for s in scs]
+        st = torch.cuda.Stream()
+        subsets = []
+        for k in range(24):
+            m = rng.random(len(scs)) < 0.5
+            m[k % len(scs)] = True
+            subsets.append(np.flatnonzero(m))
+        for rep in range(2):
+            for sub in subsets:
+                c.step([ids[i] for i in sub], 1, st.cuda_stream)
+                steps[sub] += 1
+        got = [c.read_state(i, st.cuda_stream) for i in ids]
+    for sc, n, (pos, vel, err) in zip(scs, steps, got):
+        wpos, wvel, werr = _alone(pbdr_lib, sc, int(n), streaming)
+        assert err == werr == 0
+        assert np.array_equal(pos, wpos) and np.array_equal(vel, wvel)
+
+
+@pytest.mark.parametrize("streaming", [False, True])
+def test_slot_and_range_reuse(pbdr_lib, streaming):
+    """Scenes destroyed between steps hand their slots and particle, body and
+    chunk ranges to new scenes of other sizes, while the survivors keep
+    stepping on a side stream; every scene still matches its solo run."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(32)
+    pool = [scenes.batch_scene(rng) for _ in range(14)]
+    pool.append(scenes.random_bodies_scene(seed=5, num_bodies=70))
+    with pbdr_lib.Context(0) as c:
+        c.set_path(streaming)
+        st = torch.cuda.Stream()
+        live = {}                       # sid -> (pool index, steps)
+        results = []
+        nxt = 0
+        for tick in range(12):
+            while len(live) < 5 and nxt < len(pool):
+                live[c.create_scene(pool[nxt])] = [nxt, 0]
+                nxt += 1
+            c.step(list(live), 2, st.cuda_stream)
+            for v in live.values():
+                v[1] += 2
+            if tick % 2 == 1:            # retire the two oldest
+                for sid in sorted(live, key=lambda s: live[s][0])[:2]:
+                    k, n = live.pop(sid)
+                    results.append((k, n, c.read_state(sid, st.cuda_stream)))
+                    c.destroy_scene(sid)
+        for sid, (k, n) in live.items():
+            results.append((k, n, c.read_state(sid, st.cuda_stream)))
+    assert len(results) == len(pool)
+    for k, n, (pos, vel, err) in results:
+        wpos, wvel, werr = _alone(pbdr_lib, pool[k], n, streaming)
+        assert err == werr == 0
+        assert np.array_equal(pos, wpos) and np.array_equal(vel, wvel)

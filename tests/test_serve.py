@@ -43,6 +43,11 @@ class FakeContext:
         k = self.scenes[sid]["steps"]
         return np.full((n, 3), k, np.float32), np.zeros((n, 3), np.float32), 0
 
+    def read_states(self, ids, stream=None):
+        parts = [self.read_state(i) for i in ids]
+        return (np.concatenate([p for p, _, _ in parts]), np.concatenate([v for _, v, _ in parts]),
+                np.zeros(len(ids), np.uint32))
+
     def destroy_scene(self, sid):
         self.used -= self.scenes.pop(sid)["n"]
 
