@@ -56,9 +56,9 @@ def parse_args():
     ap.add_argument("--cpu-substeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample-scenes", type=int, default=256)
-    ap.add_argument("--serve-seconds", type=float, default=0.5,
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the Poisson arrival trace of the serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
     ap.add_argument("--settle", type=int, default=240,
@@ -256,6 +256,9 @@ def run_pbdr(args, rank, world, local_rank):
             clocks.start()
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
+        # cudaProfilerStart/Stop bracket the timed region, so that a profiler
+        # started with collection off sees exactly its launches
+        torch.cuda.profiler.start()
         t_start.record(stream)
         for k in range(args.steps):
             ev[k][0].record(stream)
@@ -263,6 +266,7 @@ def run_pbdr(args, rank, world, local_rank):
             ev[k][1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         barrier()
         clk = clocks.stop() if clocks else None
         ms_total = t_start.elapsed_time(t_end)

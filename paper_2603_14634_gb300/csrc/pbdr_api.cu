@@ -142,6 +142,7 @@ struct Plan {
   uint64_t graph_gen = 0;          // context buffer generation the graph saw
   int64_t graph_launches = 0;
   uint64_t last_use = 0;           // for least-recently-used eviction
+  int64_t substeps_run = 0;
   Plan() = default;
   Plan(const Plan &) = delete;
   Plan &operator=(const Plan &) = delete;
@@ -150,7 +151,8 @@ struct Plan {
   }
 };
 
-constexpr size_t kMaxCachedPlans = 16;
+constexpr size_t kMaxCachedPlans = 1024;
+constexpr int64_t kTuneAfter = 128;   // substeps of a plan before its launch shapes are tuned
 
 constexpr int kClassCaps[4] = {1024, 2048, 4096, 8192};
 constexpr int kClassThreads[4] = {256, 256, 512, 512};
@@ -190,6 +192,8 @@ struct pbdr_ctx {
   std::vector<BodyWrench> wh;
   std::map<std::vector<int32_t>, std::unique_ptr<Plan>> plans;
   uint64_t use_clock = 0;
+  // autotuned launch shapes by (size class, scenes in it): threads, dx, v, grid
+  std::map<std::pair<int, int32_t>, std::array<int, 4>> tune_memo;
   // tables of the active plan and the streaming form's scratch (grow-only)
   DevBuf tab, s_keys_a, s_keys_b, s_vals_a, s_vals_b, s_hist, s_cstart, s_cend, s_spos, s_pmap, s_bmap;
   const Plan *active = nullptr;
@@ -706,14 +710,37 @@ int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
 // size class are: threads per CTA (128, 256, 512), the per-particle scratch
 // (dX, x_asm) in shared or in global memory, velocities in shared memory or
 // not, and the CTAs kept per SM (the occupancy limit or half of it).  Classes
-// are tuned one after the other (largest work first) by timing whole
-// substeps of the plan - all classes running concurrently as in production -
-// with the other classes at their current shapes, and each keeps its fastest
-// shape.  The kernel's results do not depend on its launch shape, and the
+// with at least as many scenes as SMs are tuned one after the other (largest
+// work first) by timing whole substeps of the plan - all classes running
+// concurrently as in production - with the other classes at their current
+// shapes, and each keeps its fastest shape, remembered per (class, scene
+// count) for later plans.  The kernel's results do not depend on its launch shape, and the
 // state the trial substeps change is saved before and restored after, so
 // tuning has no effect on the simulation.
 int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
   int rc;
+  {  // classes with fewer scenes than SMs keep the defaults (one CTA per
+     // scene anyway); shapes tuned before for the same class and scene count
+     // are reused
+    bool todo = false;
+    for (int k = 0; k < (int)P.classes.size(); ++k) {
+      Plan::FClass &F = P.classes[k];
+      if (F.n < c->num_sms) continue;
+      auto memo = c->tune_memo.find({k, F.n});
+      if (memo == c->tune_memo.end()) {
+        todo = true;
+        continue;
+      }
+      F.threads = memo->second[0];
+      F.dx_shared = memo->second[1] != 0;
+      F.v_shared = memo->second[2] != 0;
+      F.grid = memo->second[3];
+    }
+    if (!todo) {
+      P.tuned = true;
+      return PBDR_OK;
+    }
+  }
   if (!c->dx_scratch.p && (rc = dev_alloc(c, c->dx_scratch, (size_t)c->pcap * sizeof(float4)))) return rc;
   const size_t nX = (size_t)std::max(c->np_used, 1) * sizeof(float4);
   const size_t nB = (size_t)std::max(c->nb_used, 1) * sizeof(float4);
@@ -730,17 +757,33 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
+  auto restore = [&]() -> int {
+    CUDA_TRY(cudaMemcpyAsync(c->X[0].p, sX.p, nX, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->V[0].p, sV.p, nX, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->quat.p, sQr.p, nB, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->bcom.p, sCm.p, nB, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scene_err.p, sE.p, nE, cudaMemcpyDeviceToDevice, s));
+    return PBDR_OK;
+  };
+  // every candidate starts from the same saved state: one warm substep,
+  // then the fastest of two timed pairs of substeps
   auto time_substeps = [&](float *ms) -> int {
     int64_t l = 0;
-    int r2 = fused_substep(c, P, s, l);   // warm
+    int r2 = restore();
     if (r2) return r2;
-    CUDA_TRY(cudaEventRecord(e0, s));
-    for (int rep = 0; rep < 2; ++rep)
-      if ((r2 = fused_substep(c, P, s, l))) return r2;
-    CUDA_TRY(cudaEventRecord(e1, s));
-    CUDA_TRY(cudaEventSynchronize(e1));
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    if ((r2 = fused_substep(c, P, s, l))) return r2;
+    *ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CUDA_TRY(cudaEventRecord(e0, s));
+      for (int k = 0; k < 2; ++k)
+        if ((r2 = fused_substep(c, P, s, l))) return r2;
+      CUDA_TRY(cudaEventRecord(e1, s));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      CUDA_TRY(cudaGetLastError());
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      *ms = std::min(*ms, t);
+    }
     return PBDR_OK;
   };
   // classes by descending particle count
@@ -753,6 +796,7 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
   std::sort(work.begin(), work.end());
   for (auto &wk : work) {
     Plan::FClass &F = P.classes[wk.second];
+    if (F.n < c->num_sms || c->tune_memo.count({wk.second, F.n})) continue;
     float best = 1e30f;
     int bt = F.threads, bg = F.grid;
     bool bv = F.v_shared, bd = F.dx_shared;
@@ -789,14 +833,11 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
     F.v_shared = bv;
     F.dx_shared = bd;
     F.grid = bg;
+    c->tune_memo[{wk.second, F.n}] = {bt, bd ? 1 : 0, bv ? 1 : 0, bg};
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  CUDA_TRY(cudaMemcpyAsync(c->X[0].p, sX.p, nX, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->V[0].p, sV.p, nX, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->quat.p, sQr.p, nB, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->bcom.p, sCm.p, nB, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->scene_err.p, sE.p, nE, cudaMemcpyDeviceToDevice, s));
+  if ((rc = restore())) return rc;
   CUDA_TRY(cudaStreamSynchronize(s));
   for (DevBuf *b : {&sX, &sV, &sQr, &sCm, &sE}) dev_free(c, *b);
   P.tuned = true;
@@ -1241,21 +1282,24 @@ int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, v
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = activate(c, P, s))) return rc;
   int64_t launches = 0;
-  if (substeps > 0 && P->fused && c->autotune && !P->tuned) {
-    rc = autotune_fused(c, *P, s);
-    if (rc) return rc;
-  }
   const bool graphs = c->use_graphs && !c->profiling && s != nullptr && substeps > 0;
   if (graphs && P->graph && P->graph_gen != c->gen) {   // a buffer it uses has moved
     cudaGraphExecDestroy(P->graph);
     P->graph = nullptr;
   }
-  if (graphs && !P->graph) {
-    rc = capture_plan(c, *P, s);
-    if (rc) return rc;
-    P->graph_gen = c->gen;
-  }
   for (int32_t k = 0; k < substeps; ++k) {
+    // launch shapes are tuned once the plan has run kTuneAfter substeps,
+    // on a state where contacts have formed
+    if (P->fused && c->autotune && !P->tuned && P->substeps_run >= kTuneAfter) {
+      if ((rc = autotune_fused(c, *P, s))) return rc;
+      if (P->graph) cudaGraphExecDestroy(P->graph);
+      P->graph = nullptr;
+    }
+    if (graphs && !P->graph) {
+      if ((rc = capture_plan(c, *P, s))) return rc;
+      P->graph_gen = c->gen;
+    }
+    ++P->substeps_run;
     if (graphs) {
       CUDA_TRY(cudaGraphLaunch(P->graph, s));
       launches += P->graph_launches;

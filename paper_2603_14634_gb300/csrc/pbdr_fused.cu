@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       Xs[i] = make_float4(xt.x, xt.y, xt.z, x.w);
       Vl[i] = make_float4(vt.x, vt.y, vt.z, 0.f);
     }
+    __syncthreads();   // the body passes below read x~ of particles other threads wrote
 
     // ---- neighbour lists ---------------------------------------------------
     // Only "interface" particles can be in a pair: p within R_n of q puts p

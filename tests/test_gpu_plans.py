@@ -85,3 +85,32 @@ def test_slot_and_range_reuse(pbdr_lib, streaming):
         wpos, wvel, werr = _alone(pbdr_lib, pool[k], n, streaming)
         assert err == werr == 0
         assert np.array_equal(pos, wpos) and np.array_equal(vel, wvel)
+
+
+def test_two_contexts_in_lockstep_stay_identical(pbdr_lib):
+    """Two contexts step the same 340 scenes (plus one scene for the
+    streaming kernels, whose launches leave other data in shared memory
+    between the scene-resident launches) one substep at a time; their states
+    must stay bit-identical.  A missing barrier between the integration and
+    the bounding-box pass once made rare neighbour lists depend on stale
+    shared memory, which this catches."""
+    rng = np.random.default_rng(8)
+    scs = [scenes.batch_scene(rng) for _ in range(340)]
+    scs.append(scenes.random_bodies_scene(seed=3, num_bodies=75))
+    ctxs = []
+    try:
+        for _ in range(2):
+            c = pbdr_lib.Context(0)
+            c.set_option(pbdr_lib.OPT_GRAPHS, 0)
+            c.set_option(pbdr_lib.OPT_AUTOTUNE, 0)
+            ctxs.append((c, [c.create_scene(s) for s in scs]))
+        for step in range(1, 201):
+            for c, ids in ctxs:
+                c.step(ids, 1)
+            if step % 10 == 0:
+                a = ctxs[0][0].read_states(ctxs[0][1])
+                b = ctxs[1][0].read_states(ctxs[1][1])
+                assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), f"substep {step}"
+    finally:
+        for c, _ in ctxs:
+            c.close()

@@ -388,13 +388,15 @@ def test_empty_and_single_particle_scene(ctx, orc):
 def test_graph_replay_and_autotune_are_bit_identical(pbdr_lib, streaming):
     """A captured CUDA graph per substep and the launch-shape autotuner change
     nothing in the results: plain launches, graph replay and graph replay
-    after tuning give identical bytes (scenes of every size class plus one
-    larger scene that takes the streaming kernels)."""
+    with tuning give identical bytes.  340 scenes fill the small size
+    classes past the SM count (so they are tuned) and one larger scene takes
+    the streaming kernels; the tuning starts inside the second call, after
+    128 substeps, and the graph is captured again after it."""
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(8)
-    scs = [scenes.batch_scene(rng) for _ in range(10)]
+    scs = [scenes.batch_scene(rng) for _ in range(340)]
     scs.append(scenes.random_bodies_scene(seed=3, num_bodies=75))   # 9375 particles
-    outs = []
+    outs, cfgs = [], []
     for graphs, tune in ((0, 0), (1, 0), (1, 1)):
         with pbdr_lib.Context(0) as c:
             c.set_path(streaming)
@@ -403,8 +405,11 @@ def test_graph_replay_and_autotune_are_bit_identical(pbdr_lib, streaming):
             ids = [c.create_scene(s) for s in scs]
             st = torch.cuda.Stream()
             c.step(ids, 7, st.cuda_stream)
-            c.step(ids, 5, st.cuda_stream)
+            c.step(ids, 130, st.cuda_stream)
             outs.append([c.read_state(i, st.cuda_stream)[:2] for i in ids])
+            cfgs.append(c.plan_config(ids))
+    if not streaming:
+        assert any(k["scenes"] >= 152 for k in cfgs[2])   # a class was large enough to tune
     for other in outs[1:]:
         for (p0, v0), (p1, v1) in zip(outs[0], other):
             assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
