@@ -184,12 +184,19 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_sha():
-    """hash of every CUDA source of the library (a changed kernel voids the
-    committed ncu traffic figures)"""
+# the sources each timed kernel is compiled from
+KERNEL_SOURCES = {
+    "k_scene_substep": ("pbdr_fused.cu", "pbdr_math.cuh", "pbdr_internal.cuh"),
+    "k_iterate": ("pbdr_kernels.cu", "pbdr_math.cuh", "pbdr_internal.cuh"),
+}
+
+
+def kernel_source_sha(kernel):
+    """hash of the CUDA sources of one kernel (a changed kernel voids its
+    committed ncu traffic figure)"""
     h = hashlib.sha256()
-    for src in sorted(glob.glob(os.path.join(ROOT, "paper_2603_14634_gb300", "csrc", "*.cu*"))):
-        with open(src, "rb") as f:
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2603_14634_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -198,7 +205,7 @@ def ncu_traffic(kernel):
     """DRAM bytes per unit (particle-iteration or particle-substep) of a
     kernel from the committed ncu summary, if it was taken on the current
     kernel sources."""
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     for path in glob.glob(os.path.join(ROOT, "profiles", f"*{kernel}*.md")):
         txt = open(path).read()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
