@@ -4,8 +4,8 @@
  * PBD-R ("Physically Accurate Rigid-Body Dynamics in Particle-Based
  * Simulation", arXiv 2603.14634) steps rigid bodies made of equal spheres
  * ("particles") with position-based dynamics.  One substep is Algorithm 1:
- *   - integration:  v~ = v + dt w f_ext(x),  x~ = x + dt v~       (Alg. 1, l.1-4)
- *   - K solver iterations, each:                                    (Alg. 1, l.5-11)
+ *   - integration:  v~ = v + dt w f_ext(x),  x~ = x + dt v~       (Alg. 1, integration)
+ *   - K solver iterations, each:                                    (Alg. 1, solver loop)
  *       ground contact dX_PG and particle-particle contact dX_PP between
  *       particles of different bodies, with Coulomb friction (Sec. III-A),
  *       shape matching dX_SM toward the best rigid fit of the rest shape
@@ -110,7 +110,7 @@ int pbdr_create_scene(pbdr_ctx *ctx, const pbdr_scene_desc *desc, pbdr_scene *ou
 int pbdr_destroy_scene(pbdr_ctx *ctx, pbdr_scene scene);
 
 /* Sets a constant external force F (N) at the centre of mass and a constant
- * torque tau (N m) about it on one body (the f_ext of Alg. 1 line 2 for the
+ * torque tau (N m) about it on one body (the f_ext of the integration step of Alg. 1, for the
  * pushed-box and box-with-torque tests of Table I).  Each particle receives
  * F/M + alpha x (x - c) with alpha = I^-1 tau, c and I taken at the start of
  * the substep.  Zero F and tau remove the wrench.  Synchronous. */

@@ -371,7 +371,7 @@ void orc_enforce_momentum(int32_t n, const double *mass, const double *xb,
 }
 
 /* ------------------------------------------------------------------------ */
-/* contacts (Sec. III-A constraints (1) and (2), Algorithm 1 lines 5-6).     */
+/* contacts (Sec. III-A constraints (1) and (2); contact step of Algorithm 1).  */
 /* The paper gives no formulas; this is standard position-based contact with */
 /* Coulomb friction: normal push-out by the penetration, friction removes    */
 /* the tangential displacement of this substep up to mu times the            */
@@ -446,7 +446,7 @@ int orc_substep(const orc_scene *s, double *x, double *v, double *rot, int use_b
   for (int32_t b = 0; b < B; ++b)
     for (int32_t p = s->body_off[b]; p < s->body_off[b + 1]; ++p) body[p] = b;
 
-  /* integration step (Alg. 1 lines 1-4): v~ = v_init + dt w f_ext(x),
+  /* integration step (integration step of Algorithm 1): v~ = v_init + dt w f_ext(x),
    * x~ = x_init + dt v~.  Gravity gives w m g = g.  A constant force F at the
    * CoM gives every particle F/M; a constant torque tau gives the rigid angular
    * acceleration alpha = I^-1 tau, i.e. alpha x (x_init - c), with c and I of
@@ -498,7 +498,7 @@ int orc_substep(const orc_scene *s, double *x, double *v, double *rot, int use_b
     }
   }
 
-  /* solver iterations (Alg. 1 lines 5-11) */
+  /* solver iterations (solver loop of Algorithm 1) */
   for (int32_t it = 0; it < s->iterations; ++it) {
     /* contacts from X_i (Jacobi): dX_PG + dX_PP */
     for (int32_t p = 0; p < N; ++p) {

@@ -4,20 +4,23 @@
 // size class (persistent kernel, scenes handed out largest first).
 //
 // Shared memory per CTA (NCAP = particle capacity of the class):
-//   Xs  float4[NCAP]  x (predicted, then X_i), w
-//   DXs float4[NCAP]  contact correction dX_c, later x_asm   (or global scratch)
+//   Xs    float4[NCAP]  x~, then X_i; w = 1/m, negative for particles that
+//                       have contact candidates
+//   DXs   float4[NCAP]  contact correction dX, later x_asm (or global scratch)
 //   build area, aliased with DXs while the neighbour lists are built:
-//     start u32[T'+1]  bucket counts -> starts (T' = smallest power of two >= N)
-//     sidx  u16[N]     particle indices sorted by bucket
-//     lbody u16[N]     body index of every particle within the scene
-// Velocities, rest offsets and neighbour lists stay in global memory; within
-// one CTA's processing of a scene they are L2 resident.
+//     lbody u16[N] body of every particle, slist u16 interface particles,
+//     sidx u16 interface particles by bucket, start u32[T+1] buckets,
+//     cand u8 per interface particle
+//   V     float4[NCAP]  velocities (or in global memory)
+//   partials            chunk sums (or in global memory)
+// Rest offsets, neighbour lists and the per-body scratch stay in global
+// memory, L2-resident while a CTA works on a scene.
 //
-// The neighbour lists are the same sets as the streaming path's (every pair
+// The neighbour lists are the same sets as the streaming form's (every pair
 // within R_n by the same FP32 predicate, ascending), so the contact sums run
-// in the same order.  Inside a body, lane l owns particles l, l+32, ... and the
-// body sums use the same shuffle tree, so a scene's result does not depend on
-// which other scenes share the launch.
+// in the same order.  Chunks of a body are summed in chunk order by its owner
+// warp and every warp reduction is a fixed shuffle tree, so a scene's result
+// depends neither on the other scenes of the launch nor on the launch shape.
 #include <math.h>
 
 #include "pbdr_internal.cuh"

@@ -2,7 +2,7 @@
 
 The paper needs, for the particle-particle contact constraint, the pairs of
 particles of *different object groups* that may touch (Sec. III-A, constraint
-(2); Algorithm 1 line 6) but does not say how they are found.  The oracle's
+(2); the particle contact step of Algorithm 1) but does not say how they are found.  The oracle's
 definition is the O(N^2) FP32 predicate; its hashed-grid search must return
 exactly the same sets, and both are checked against an independent library
 range query (scipy's k-d tree in FP64) away from the rounding band at R_n.

@@ -21,7 +21,7 @@ def _free_space(sc):
 
 
 def test_free_fall_discrete_closed_form(orc):
-    """No contact: Algorithm 1 lines 1-3 alone, so v_n = v_0 + n g dt and
+    """No contact: the integration step of Algorithm 1 alone, so v_n = v_0 + n g dt and
     x_n = x_0 + n dt v_0 + g dt^2 n(n+1)/2 (symplectic Euler)."""
     sc = scenes.cube_drop(clearance=50.0)
     sc.vel[:] = np.array([0.3, -0.2, 1.5], np.float32)
