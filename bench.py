@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
+    ap.add_argument("--grad-steps", type=int, default=200,
+                    help="substeps of the differentiated 16-body run (0: skip)")
     ap.add_argument("--settle", type=int, default=240,
                     help="substeps run before the warm-up so that bodies have landed and touch")
     a = ap.parse_args()
@@ -433,6 +435,8 @@ def run_pbdr(args, rank, world, local_rank):
     }
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args, local_rank)
+    if world == 1 and args.grad_steps > 0:
+        line["gradient"] = run_gradient(args, local_rank)
     if world == 1 and not args.no_cpu_baseline:
         cpu_scs = scs[: args.cpu_scenes]
         thr = host_cores()
@@ -445,6 +449,35 @@ def run_pbdr(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+def run_gradient(args, local_rank):
+    """Differentiation: d(final body centres of mass)/d(initial rigid
+    velocities v_b, omega_b) of 16 bodies of 5^3 sliding on the ground
+    (4x4 grid, 0.6 m pitch, mu = 0.5, K = 10, dt = 1/240), by forward-mode
+    tangents: the 96 directions run as 96 copies of the scene in one
+    batched tangent step."""
+    import numpy as np
+    import torch
+    from paper_2603_14634_gb300 import diff
+    from paper_2603_14634_gb300.binding import Context
+    sc = diff.c5_scene(seed=args.seed)
+    v = np.stack([sc.vel[s].astype(np.float64).mean(0) for s in diff.body_slices(sc)])
+    w = np.zeros_like(v)
+    with Context(local_rank) as c:
+        diff.final_com_and_jacobian(c, sc, v, w, 3)        # warm: build, allocate
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, J = diff.final_com_and_jacobian(c, sc, v, w, args.grad_steps)
+        secs = time.perf_counter() - t0
+    dirs = J.shape[1]
+    return {
+        "what": "d(final body CoMs)/d(initial v_b, omega_b), 16 bodies of 5^3, forward-mode tangents, all directions batched",
+        "outputs": int(J.shape[0]), "directions": int(dirs), "substeps": args.grad_steps,
+        "ms": round(secs * 1e3, 2),
+        "tangent_particle_iters_per_s": round(dirs * sc.num_particles * sc.iterations * args.grad_steps / secs, 1),
+        "timing": "wall clock around the whole call (scene copies, seeds, tangent steps, read-back)",
+    }
 
 
 def run_serving(args, local_rank):

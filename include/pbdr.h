@@ -196,6 +196,38 @@ int pbdr_read_neighbors(pbdr_ctx *ctx, pbdr_scene scene, uint32_t *sorted_key,
 #define PBDR_OPT_AUTOTUNE 4
 int pbdr_set_option(pbdr_ctx *ctx, int32_t option, int64_t value);
 
+/* Tangent-linear (forward-mode) substeps: the derivative of Algorithm 1's
+ * map from the state at the start of a substep to the state at its end,
+ * along a direction given per particle (dX, dV).  pbdr_step_tangent advances
+ * the scenes ids[0..n) by `substeps` substeps of the streaming form (the
+ * primal state exactly as pbdr_step with PBDR_OPT_PATH = 1 advances it) and
+ * their tangents with them: prediction x~' = x' + dt v', then per iteration
+ * the derivative of the contacts with friction (Sec. III-A (1), (2)), of
+ * shape matching including the rotation (from the polar decomposition
+ * A = R S: dR = R [w]x with (tr(S) I - S) w = axial(R^T dA - dA^T R)), of the
+ * velocity update (Sec. III-B) and of the momentum constraint (Sec. III-C,
+ * Eqs. lin_momentum / ang_momentum, including the change of the inertia
+ * tensor).  The neighbour lists, the contact set and the sticking/sliding
+ * branch of every friction term are the primal's (the tangent is the
+ * derivative inside those pieces).  Scenes with a body wrench or with
+ * PBDR_STD_VELOCITY / PBDR_SM_FROM_XI give PBDR_ERR_UNSUPPORTED.
+ * Tangent storage (4 float4 per particle) is allocated on first use; new
+ * scenes start with zero tangents.  Asynchronous on `stream`.
+ * Errors: PBDR_ERR_INVALID, PBDR_ERR_UNSUPPORTED, PBDR_ERR_OOM,
+ * PBDR_ERR_BUDGET, PBDR_ERR_CUDA. */
+int pbdr_step_tangent(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int32_t substeps,
+                      void *stream);
+
+/* Sets the tangent of one scene: dpos, dvel host [N*3] in the caller's
+ * particle order (NULL = zero).  Stream-ordered on `stream`; the host
+ * buffers must stay valid until the stream reaches this point. */
+int pbdr_write_tangent(pbdr_ctx *ctx, pbdr_scene scene, const float *dpos, const float *dvel,
+                       void *stream);
+
+/* Reads the tangent of one scene into host [N*3] arrays (NULL = skip) and
+ * synchronises `stream`.  PBDR_ERR_INVALID before any tangent exists. */
+int pbdr_read_tangent(pbdr_ctx *ctx, pbdr_scene scene, float *dpos, float *dvel, void *stream);
+
 /* Launch shapes of the scene-resident kernel for the scene set ids[0..n):
  * out[5k..5k+4] = {particle capacity, scenes, threads per CTA, scratch bits
  * (1: velocities in shared memory, 2: per-particle scratch in shared memory),

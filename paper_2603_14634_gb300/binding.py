@@ -31,6 +31,7 @@ EXPORTS = [
     "pbdr_build_neighbors", "pbdr_read_neighbors", "pbdr_last_launch_count",
     "pbdr_neighbor_total", "pbdr_set_profiling", "pbdr_read_profile",
     "pbdr_neighbors_noalloc", "pbdr_set_option", "pbdr_plan_config",
+    "pbdr_step_tangent", "pbdr_write_tangent", "pbdr_read_tangent",
 ]
 NUM_STAGES = 6
 STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate", "scene_resident")
@@ -87,6 +88,9 @@ def load(path: Optional[str] = None):
     L.pbdr_write_state.argtypes = [vp, i32, vp, vp, vp]
     L.pbdr_read_states.argtypes = [vp, P(i32), i32, vp, vp, vp, vp]
     L.pbdr_write_states.argtypes = [vp, P(i32), i32, vp, vp, vp]
+    L.pbdr_step_tangent.argtypes = [vp, P(i32), i32, i32, vp]
+    L.pbdr_write_tangent.argtypes = [vp, i32, vp, vp, vp]
+    L.pbdr_read_tangent.argtypes = [vp, i32, vp, vp, vp]
     L.pbdr_scene_info.argtypes = [vp, i32, P(i32), P(i32)]
     L.pbdr_last_error.argtypes = []
     L.pbdr_last_error.restype = C.c_char_p
@@ -190,6 +194,26 @@ def pbdr_set_body_wrench(ctx: int, scene: int, body: int, F, tau) -> None:
 def pbdr_step(ctx: int, ids: Sequence[int], substeps: int = 1, stream=None) -> None:
     arr, p = _ids(ids)
     _check(load().pbdr_step(ctx, p, len(arr), substeps, _stream(stream)))
+
+
+def pbdr_step_tangent(ctx: int, ids: Sequence[int], substeps: int = 1, stream=None) -> None:
+    arr, p = _ids(ids)
+    _check(load().pbdr_step_tangent(ctx, p, len(arr), substeps, _stream(stream)))
+
+
+def pbdr_write_tangent(ctx: int, scene: int, dpos=None, dvel=None, stream=None) -> None:
+    dpos = None if dpos is None else np.ascontiguousarray(dpos, dtype=np.float32)
+    dvel = None if dvel is None else np.ascontiguousarray(dvel, dtype=np.float32)
+    _check(load().pbdr_write_tangent(ctx, scene, _ptr(dpos), _ptr(dvel), _stream(stream)))
+
+
+def pbdr_read_tangent(ctx: int, scene: int, stream=None):
+    """-> (dpos [N,3], dvel [N,3])"""
+    n, _ = pbdr_scene_info(ctx, scene)
+    dpos = np.empty((n, 3), np.float32)
+    dvel = np.empty((n, 3), np.float32)
+    _check(load().pbdr_read_tangent(ctx, scene, _ptr(dpos), _ptr(dvel), _stream(stream)))
+    return dpos, dvel
 
 
 def pbdr_scene_info(ctx: int, scene: int):
@@ -347,6 +371,17 @@ class Context:
 
     def write_states(self, ids, pos=None, vel=None, stream=None):
         pbdr_write_states(self.h, ids, pos, vel, stream)
+
+    def step_tangent(self, ids, substeps: int = 1, stream=None):
+        if isinstance(ids, (int, np.integer)):
+            ids = [int(ids)]
+        pbdr_step_tangent(self.h, ids, substeps, stream)
+
+    def write_tangent(self, sid: int, dpos=None, dvel=None, stream=None):
+        pbdr_write_tangent(self.h, sid, dpos, dvel, stream)
+
+    def read_tangent(self, sid: int, stream=None):
+        return pbdr_read_tangent(self.h, sid, stream)
 
     def build_neighbors(self, ids, stream=None):
         if isinstance(ids, (int, np.integer)):

@@ -175,6 +175,7 @@ struct pbdr_ctx {
   RangeAlloc pa, ba, ca;               // free ranges of particles, bodies, chunks
   int nbr_cap = 32;
   DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
+  DevBuf Xd[2], Vd[2];             // tangents of X, V (forward-mode derivative), lazily allocated
   DevBuf bodies, wrench, quat, bcom, biter, border;
   DevBuf dx_scratch, tickets, chunks, partials;
   int32_t ccap = 0, nc_used = 0;   // chunk (and partial-slot) capacity / use
@@ -683,6 +684,76 @@ int ensure_class_streams(pbdr_ctx *c) {
 
 int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches);
 
+// tangent buffers sized to the particle capacity; new space is zero
+int ensure_tangent(pbdr_ctx *c) {
+  const size_t bytes = (size_t)std::max(c->pcap, 1) * sizeof(float4);
+  for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]}) {
+    if (b->bytes >= bytes) continue;
+    const size_t old = b->p ? std::min(b->bytes, (size_t)c->np_used * sizeof(float4)) : 0;
+    int rc = dev_grow(c, *b, bytes, old);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemset(b->as<unsigned char>() + old, 0, bytes - old));
+  }
+  return PBDR_OK;
+}
+
+// one substep of a streaming plan with the tangent (forward-mode) kernels
+int tangent_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
+  if (P.np == 0) return PBDR_OK;
+  const int K = P.kmax;
+  float4 *X0 = c->X[0].as<float4>(), *V0 = c->V[0].as<float4>();
+  float4 *X1 = c->X[1].as<float4>(), *V1 = c->V[1].as<float4>();
+  float4 *D0 = c->Xd[0].as<float4>(), *W0 = c->Vd[0].as<float4>();
+  float4 *D1 = c->Xd[1].as<float4>(), *W1 = c->Vd[1].as<float4>();
+  const bool odd = K % 2 == 1;
+  float4 *Xp = odd ? X1 : X0, *Vp = odd ? V1 : V0, *Dp = odd ? D1 : D0, *Wp = odd ? W1 : W0;
+  launches += launch_predict(predict_args(c, P, X0, V0, Xp, Vp, 1), s);
+  TangentPredictArgs tp{};
+  tp.Xd0 = D0;
+  tp.Vd0 = W0;
+  tp.Xdp = Dp;
+  tp.Vdp = Wp;
+  tp.pbody = c->pbody.as<int32_t>();
+  tp.bodies = c->bodies.as<BodyRec>();
+  tp.scenes = c->scenes.as<ScenePar>();
+  tp.pmap = P.pcontig ? nullptr : c->s_pmap.as<int32_t>();
+  tp.pbase = P.pbase;
+  tp.np = P.np;
+  launches += launch_predict_tangent(tp, s);
+  int rc = neighbor_stage(c, P, Xp, s, launches);
+  if (rc) return rc;
+  IterArgs ia{};
+  ia.Q = c->Q.as<float4>();
+  ia.Xinit = nullptr;
+  ia.nbr_cnt = c->nbr_cnt.as<int32_t>();
+  ia.nbr = c->nbr.as<int32_t>();
+  ia.nbr_stride = c->pcap;
+  ia.bodies = c->bodies.as<BodyRec>();
+  ia.scenes = c->scenes.as<ScenePar>();
+  ia.quat = c->quat.as<float4>();
+  ia.bcom = c->bcom.as<float4>();
+  ia.bmap = P.bcontig ? nullptr : c->s_bmap.as<int32_t>();
+  ia.bbase = P.bbase;
+  ia.nbodies = P.nb;
+  ia.scene_err = c->scene_err.as<uint32_t>();
+  for (int k = 0; k < K; ++k) {
+    const int out = (K - 1 - k) % 2;
+    ia.Xin = out ? X0 : X1;
+    ia.Vin = out ? V0 : V1;
+    ia.Xout = out ? X1 : X0;
+    ia.Vout = out ? V1 : V0;
+    ia.k = k;
+    TangentArgs ta{};
+    ta.Xdin = out ? D0 : D1;
+    ta.Vdin = out ? W0 : W1;
+    ta.Xdout = out ? D1 : D0;
+    ta.Vdout = out ? W1 : W0;
+    launches += launch_iterate_tangent(ia, ta, s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return PBDR_OK;
+}
+
 int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   int rc = ensure_class_streams(c);
   if (rc) return rc;
@@ -934,7 +1005,7 @@ __global__ void k_errs(uint32_t *scene_err, const int32_t *ids, int32_t n, uint3
 // gather / scatter of xyz state for scenes ids[0..n) through device staging
 int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, float *hvel,
                     const float *cpos, const float *cvel, uint32_t *err_bits, int unpack,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool tangent = false) {
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
   std::vector<int32_t> p0(n);
@@ -956,8 +1027,8 @@ int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, 
   CUDA_TRY(cudaMemcpyAsync(c->seg_p0.p, p0.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(c->seg_off.p, off.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
   PackArgs pa{};
-  pa.X = c->X[0].as<float4>();
-  pa.V = c->V[0].as<float4>();
+  pa.X = tangent ? c->Xd[0].as<float4>() : c->X[0].as<float4>();
+  pa.V = tangent ? c->Vd[0].as<float4>() : c->V[0].as<float4>();
   pa.hpos = want_pos ? c->stage_pos.as<float>() : nullptr;
   pa.hvel = want_vel ? c->stage_vel.as<float>() : nullptr;
   pa.seg_p0 = c->seg_p0.as<int32_t>();
@@ -1212,6 +1283,11 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   }
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
+  if (c->Xd[0].p && N > 0) {   // tangents in use: the new scene starts with zero tangents
+    if ((rc = ensure_tangent(c))) return rc;
+    for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]})
+      CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
+  }
   if ((int32_t)c->bh.size() < B0 + B) {
     c->bh.resize(B0 + B);
     c->wh.resize(B0 + B);
@@ -1346,6 +1422,53 @@ int pbdr_write_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, const float
                       void *stream) {
   g_err.clear();
   return transfer_states(c, ids, n, nullptr, nullptr, pos, vel, nullptr, 1, (cudaStream_t)stream);
+}
+
+int pbdr_step_tangent(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, void *stream) {
+  g_err.clear();
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  if (substeps < 0) return fail(PBDR_ERR_INVALID, "substeps must be >= 0");
+  int rc = check_ids(c, ids, n);
+  if (rc) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    const SceneHost &S = c->sh[ids[i]];
+    if (S.wrench_bodies) return fail(PBDR_ERR_UNSUPPORTED, "tangent substeps of scenes with a body wrench");
+    if (S.par.flags & (kStdVelocity | PBDR_SM_FROM_XI))
+      return fail(PBDR_ERR_UNSUPPORTED, "tangent substeps with PBDR_STD_VELOCITY or PBDR_SM_FROM_XI");
+  }
+  Plan *P = nullptr;
+  if ((rc = build_plan(c, ids, n, &P, 1))) return rc;
+  if ((rc = ensure_tangent(c))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = activate(c, P, s))) return rc;
+  int64_t launches = 0;
+  for (int32_t k = 0; k < substeps; ++k)
+    if ((rc = tangent_substep(c, *P, s, launches))) return rc;
+  c->last_launches = launches;
+  return PBDR_OK;
+}
+
+int pbdr_write_tangent(pbdr_ctx *c, pbdr_scene s, const float *dpos, const float *dvel, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if ((rc = ensure_tangent(c))) return rc;
+  const SceneHost &S = c->sh[s];
+  if (S.np == 0) return PBDR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (DevBuf *b : {&c->Xd[0], &c->Vd[0]})
+    CUDA_TRY(cudaMemsetAsync(b->as<float4>() + S.p0, 0, (size_t)S.np * sizeof(float4), st));
+  if (!dpos && !dvel) return PBDR_OK;
+  return transfer_states(c, &s, 1, nullptr, nullptr, dpos, dvel, nullptr, 1, st, true);
+}
+
+int pbdr_read_tangent(pbdr_ctx *c, pbdr_scene s, float *dpos, float *dvel, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (!c->Xd[0].p) return fail(PBDR_ERR_INVALID, "no tangent has been written");
+  if (c->sh[s].np == 0) return PBDR_OK;
+  return transfer_states(c, &s, 1, dpos, dvel, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream, true);
 }
 
 int pbdr_scene_info(pbdr_ctx *c, pbdr_scene s, int32_t *np, int32_t *nb) {

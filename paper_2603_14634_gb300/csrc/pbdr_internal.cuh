@@ -168,6 +168,24 @@ struct FusedLayout {
   size_t v_off, part_off, bytes;
 };
 
+// Tangent (forward-mode derivative) of the streaming form: dX, dV per
+// particle, double-buffered like X, V.  The neighbour lists and the branch
+// of every contact and friction test are those of the primal state.
+struct TangentArgs {
+  const float4 *Xdin, *Vdin;
+  float4 *Xdout, *Vdout;
+};
+
+struct TangentPredictArgs {
+  const float4 *Xd0, *Vd0; // tangents at the start of the substep
+  float4 *Xdp, *Vdp;       // tangents of x~, v~ (may alias)
+  const int32_t *pbody;
+  const BodyRec *bodies;
+  const ScenePar *scenes;
+  const int32_t *pmap;
+  int32_t pbase, np;
+};
+
 struct WrenchArgs {
   const float4 *X, *Q;
   const BodyRec *bodies;
@@ -191,6 +209,8 @@ int launch_predict(const PredictArgs &a, cudaStream_t s);
 int launch_cells(const CellArgs &a, cudaStream_t s);
 int launch_neighbors(const NbrArgs &a, cudaStream_t s);
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
+int launch_iterate_tangent(const IterArgs &a, const TangentArgs &t, cudaStream_t s);
+int launch_predict_tangent(const TangentPredictArgs &a, cudaStream_t s);
 int launch_wrench(const WrenchArgs &a, cudaStream_t s);
 int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
 int launch_expand_map(const int32_t *seg_start, const int32_t *seg_base, int32_t nseg, int32_t *map,

@@ -7,11 +7,11 @@
 // Bodies are contiguous particle ranges; scenes are contiguous body ranges.
 //
 // Kernels of one substep (Algorithm 1):
-//   k_predict   integration (l.1-4) and the hashed-grid cell key of x~
+//   k_predict   integration and the hashed-grid cell key of x~
 //   (radix sort of (key, particle))
 //   k_cells     bucket [start, end) ranges and positions in sorted order
 //   k_neighbors candidate lists N(p) with the exact FP32 predicate (ELL)
-//   k_iterate   one solver iteration (l.5-10) for one body per warp:
+//   k_iterate   one solver iteration for one body per warp:
 //               contacts -> X_bsm, V_bsm; shape matching -> X_asm, V_asm;
 //               momentum enforcement -> X_{i+1}, V_{i+1}
 #include <math.h>
@@ -378,6 +378,303 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Tangent-linear substep (forward-mode derivative of Algorithm 1).
+//
+// Beside the primal state (X, V) every particle carries a tangent (dX, dV):
+// the derivative of its state along one direction of the initial state.
+// The kernels below advance both; the primal arithmetic is k_iterate's.  The
+// contact set, the neighbour lists and the sticking / sliding branch of
+// every friction term are those of the primal state (their derivative is
+// taken inside the branch).  The rotation's tangent follows from the polar
+// decomposition A = R S: with dR = R [w]x,
+//   (tr(S) I - S) w = axial(R^T dA - dA^T R)
+// (S = R^T A symmetric).  The momentum correction's tangent differentiates
+// dv = (P_bsm - P_asm)/M and w = I^-1 (L_asm - L_bsm), including dI.
+// ---------------------------------------------------------------------------
+
+// derivative of friction_cut(del, n, mp) along (del', n', mp')
+__device__ __forceinline__ float3 friction_cut_d(float3 del, float3 del_d, float3 n, float3 n_d, float mp,
+                                                 float mp_d) {
+  const float dn = dot(del, n);
+  const float dn_d = dot(del_d, n) + dot(del, n_d);
+  const float3 t = del - dn * n;
+  const float3 t_d = del_d - dn_d * n - dn * n_d;
+  const float lt = sqrtf(dot(t, t));
+  if (!(lt > 0.f)) return make_float3(0.f, 0.f, 0.f);
+  const float f = mp / lt;
+  if (!(f < 1.f)) return t_d;                     // sticking: the whole tangential step
+  const float lt_d = dot(t, t_d) / lt;
+  return (mp_d / lt - f * lt_d / lt) * t + f * t_d;   // sliding: mu pen along t/|t|
+}
+
+__device__ __forceinline__ float3 contact_dx_d(const IterArgs &a, const TangentArgs &t, const ScenePar &sp,
+                                               int32_t p, float4 xp, float4 vp, float3 xpd, float3 vpd) {
+  const float r = sp.radius, d_c = 2.f * r, mu = sp.friction, dt = sp.dt;
+  const float3 n = make_float3(sp.nx, sp.ny, sp.nz);
+  const float3 zero = make_float3(0.f, 0.f, 0.f);
+  float3 dXd = zero;
+  const float pen_g = r - (dot(n, f3(xp)) - sp.nd);
+  if (pen_g > 0.f) {
+    const float pen_d = -dot(n, xpd);
+    dXd = pen_d * n - friction_cut_d(dt * f3(vp), dt * vpd, n, zero, mu * pen_g, mu * pen_d);
+  }
+  const int32_t cnt = a.nbr_cnt[p];
+  float3 acc = zero;
+  int active = 0;
+  for (int32_t j = 0; j < cnt; ++j) {
+    const int32_t q = a.nbr[(int64_t)j * a.nbr_stride + p];
+    const float4 xq = a.Xin[q];
+    const float3 diff = f3(xp) - f3(xq);
+    const float dd = dot(diff, diff);
+    if (dd > 0.f && dd < d_c * d_c) {
+      const float d = sqrtf(dd);
+      const float pen = d_c - d;
+      const float3 nh = (1.f / d) * diff;
+      const float3 diff_d = xpd - f3(t.Xdin[q]);
+      const float d_d = dot(nh, diff_d);
+      const float3 nh_d = (1.f / d) * (diff_d - d_d * nh);
+      const float4 vq = a.Vin[q];
+      const float s = xp.w / (xp.w + xq.w);
+      const float3 del = dt * (f3(vp) - f3(vq));
+      const float3 del_d = dt * (vpd - f3(t.Vdin[q]));
+      acc = acc + s * ((-d_d) * nh + pen * nh_d - friction_cut_d(del, del_d, nh, nh_d, mu * pen, -mu * d_d));
+      ++active;
+    }
+  }
+  if ((sp.flags & kContactAvg) && active > 0) acc = (1.f / (float)active) * acc;
+  return dXd + acc;
+}
+
+__global__ void __launch_bounds__(256) k_predict_tangent(TangentPredictArgs a) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
+  const ScenePar sp = a.scenes[a.bodies[a.pbody[p]].scene];
+  // v~' = v' (constant external acceleration) ; x~' = x' + dt v~'
+  const float3 vd = f3(a.Vd0[p]);
+  const float3 xd = f3(a.Xd0[p]) + sp.dt * vd;
+  a.Xdp[p] = make_float4(xd.x, xd.y, xd.z, 0.f);
+  a.Vdp[p] = make_float4(vd.x, vd.y, vd.z, 0.f);
+}
+
+// one solver iteration with its tangent, one body per warp
+__global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs t) {
+  const int lane = threadIdx.x & 31;
+  const int32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.nbodies) return;
+  const int32_t b = a.bmap ? a.bmap[w] : a.bbase + w;
+  const BodyRec br = a.bodies[b];
+  const ScenePar sp = a.scenes[br.scene];
+  const int32_t p0 = br.start, pe = br.start + br.count;
+  if (a.k >= sp.iterations) {
+    for (int32_t p = p0 + lane; p < pe; p += 32) {
+      a.Xout[p] = a.Xin[p];
+      a.Vout[p] = a.Vin[p];
+      t.Xdout[p] = t.Xdin[p];
+      t.Vdout[p] = t.Vdin[p];
+    }
+    return;
+  }
+  const float dt = sp.dt, idt = sp.inv_dt;
+  const float3 anc = f3(a.bcom[b]);   // a constant reference point: no tangent
+
+  // (1) contacts -> X_bsm, V_bsm and tangents; first sums and their tangents
+  float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
+  float tx[3] = {0.f, 0.f, 0.f}, tA[9] = {0.f}, tP[3] = {0.f, 0.f, 0.f}, tL[3] = {0.f, 0.f, 0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xp = a.Xin[p], vp = a.Vin[p];
+    const float3 xpd = f3(t.Xdin[p]), vpd = f3(t.Vdin[p]);
+    const float3 dX = contact_dx(a, sp, p, xp, vp);
+    const float3 dXd = contact_dx_d(a, t, sp, p, xp, vp, xpd, vpd);
+    const float3 xb = f3(xp) + dX;
+    const float3 vb = f3(vp) + idt * dX;
+    const float3 xbd = xpd + dXd;
+    const float3 vbd = vpd + idt * dXd;
+    a.Xout[p] = make_float4(xb.x, xb.y, xb.z, xp.w);
+    a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
+    t.Xdout[p] = make_float4(xbd.x, xbd.y, xbd.z, 0.f);
+    t.Vdout[p] = make_float4(vbd.x, vbd.y, vbd.z, 0.f);
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 e = xb - anc;
+    const float3 me = m * e;
+    const float3 med = m * xbd;
+    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
+    sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
+    sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
+    sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
+    sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
+    const float3 l = cross(me, vb);
+    sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
+    tx[0] += med.x; tx[1] += med.y; tx[2] += med.z;
+    tA[0] += med.x * q.x; tA[1] += med.x * q.y; tA[2] += med.x * q.z;
+    tA[3] += med.y * q.x; tA[4] += med.y * q.y; tA[5] += med.y * q.z;
+    tA[6] += med.z * q.x; tA[7] += med.z * q.y; tA[8] += med.z * q.z;
+    tP[0] += m * vbd.x; tP[1] += m * vbd.y; tP[2] += m * vbd.z;
+    const float3 ld = cross(med, vb) + cross(me, vbd);
+    tL[0] += ld.x; tL[1] += ld.y; tL[2] += ld.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sx[k] = warp_sum(sx[k]); sP[k] = warp_sum(sP[k]); sL[k] = warp_sum(sL[k]);
+    tx[k] = warp_sum(tx[k]); tP[k] = warp_sum(tP[k]); tL[k] = warp_sum(tL[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    sA[k] = warp_sum(sA[k]);
+    tA[k] = warp_sum(tA[k]);
+  }
+  const float iM = br.inv_mass, M = br.mass;
+  const float3 cA = iM * make_float3(sx[0], sx[1], sx[2]);
+  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
+  const float3 Lb = make_float3(sL[0], sL[1], sL[2]) - cross(cA, Pb);
+  const float3 cAd = iM * make_float3(tx[0], tx[1], tx[2]);
+  const float3 Pbd = make_float3(tP[0], tP[1], tP[2]);
+  const float3 Lbd = make_float3(tL[0], tL[1], tL[2]) - cross(cAd, Pb) - cross(cA, Pbd);
+  float A[9], Ad[9];
+  {
+    const float qs[3] = {br.qsx, br.qsy, br.qsz};
+    const float ca[3] = {cA.x, cA.y, cA.z}, cad[3] = {cAd.x, cAd.y, cAd.z};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
+        Ad[3 * r + c] = tA[3 * r + c] - cad[r] * qs[c];
+      }
+  }
+  const float4 qrot = shape_rotation(A, a.quat[b]);
+  float R[9];
+  quat_to_mat(qrot, R);
+  // rotation tangent dR = R [wr]x from the polar decomposition
+  float3 wr;
+  {
+    float S[9], W[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        S[3 * i + j] = R[i] * A[j] + R[3 + i] * A[3 + j] + R[6 + i] * A[6 + j];      // R^T A
+        W[3 * i + j] = R[i] * Ad[j] + R[3 + i] * Ad[3 + j] + R[6 + i] * Ad[6 + j];   // R^T dA
+      }
+    const float3 ax = make_float3(W[7] - W[5], W[2] - W[6], W[3] - W[1]);   // axial(W - W^T)
+    const float s01 = 0.5f * (S[1] + S[3]), s02 = 0.5f * (S[2] + S[6]), s12 = 0.5f * (S[5] + S[7]);
+    const float tr = S[0] + S[4] + S[8];
+    solve_sym3(tr - S[0], -s01, -s02, tr - S[4], -s12, tr - S[8], ax, wr);
+  }
+
+  // (2) goals and their tangents; second sums
+  float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f}, sXX[6] = {0.f};
+  float tx2[3] = {0.f, 0.f, 0.f}, tP2[3] = {0.f, 0.f, 0.f}, tL2[3] = {0.f, 0.f, 0.f}, tXX[6] = {0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
+    const float3 xbd = f3(t.Xdout[p]), vbd = f3(t.Vdout[p]);
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 grel = make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z,
+                                    R[3] * q.x + R[4] * q.y + R[5] * q.z,
+                                    R[6] * q.x + R[7] * q.y + R[8] * q.z) + cA;
+    const float3 dsm = grel - (f3(xb4) - anc);
+    const float3 xa = f3(xb4) + dsm;
+    const float3 va = f3(vb4) + idt * dsm;
+    // g' = R (wr x q) + c'
+    const float3 wq = cross(wr, make_float3(q.x, q.y, q.z));
+    const float3 gd = make_float3(R[0] * wq.x + R[1] * wq.y + R[2] * wq.z,
+                                  R[3] * wq.x + R[4] * wq.y + R[5] * wq.z,
+                                  R[6] * wq.x + R[7] * wq.y + R[8] * wq.z) + cAd;
+    const float3 xad = gd;
+    const float3 vad = vbd + idt * (gd - xbd);
+    a.Xout[p] = make_float4(xa.x, xa.y, xa.z, xb4.w);
+    a.Vout[p] = make_float4(va.x, va.y, va.z, 0.f);
+    t.Xdout[p] = make_float4(xad.x, xad.y, xad.z, 0.f);
+    t.Vdout[p] = make_float4(vad.x, vad.y, vad.z, 0.f);
+    const float3 e = xa - anc;
+    const float3 me = m * e;
+    const float3 med = m * xad;
+    sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
+    sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
+    const float3 l = cross(me, va);
+    sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
+    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
+    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+    tx2[0] += med.x; tx2[1] += med.y; tx2[2] += med.z;
+    tP2[0] += m * vad.x; tP2[1] += m * vad.y; tP2[2] += m * vad.z;
+    const float3 ld = cross(med, va) + cross(me, vad);
+    tL2[0] += ld.x; tL2[1] += ld.y; tL2[2] += ld.z;
+    tXX[0] += 2.f * med.x * e.x; tXX[1] += med.x * e.y + me.x * xad.y; tXX[2] += med.x * e.z + me.x * xad.z;
+    tXX[3] += 2.f * med.y * e.y; tXX[4] += med.y * e.z + me.y * xad.z; tXX[5] += 2.f * med.z * e.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sx2[k] = warp_sum(sx2[k]); sP2[k] = warp_sum(sP2[k]); sL2[k] = warp_sum(sL2[k]);
+    tx2[k] = warp_sum(tx2[k]); tP2[k] = warp_sum(tP2[k]); tL2[k] = warp_sum(tL2[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    sXX[k] = warp_sum(sXX[k]);
+    tXX[k] = warp_sum(tXX[k]);
+  }
+  const float3 cA2 = iM * make_float3(sx2[0], sx2[1], sx2[2]);
+  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
+  const float3 La = make_float3(sL2[0], sL2[1], sL2[2]) - cross(cA2, Pa);
+  const float3 cA2d = iM * make_float3(tx2[0], tx2[1], tx2[2]);
+  const float3 Pad = make_float3(tP2[0], tP2[1], tP2[2]);
+  const float3 Lad = make_float3(tL2[0], tL2[1], tL2[2]) - cross(cA2d, Pa) - cross(cA2, Pad);
+  float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
+  float3 dvd = dv, omd = om;
+  if (!(sp.flags & kNoLinMom)) {
+    dv = iM * (Pb - Pa);
+    dvd = iM * (Pbd - Pad);
+  }
+  if (!(sp.flags & kNoAngMom)) {
+    const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
+                s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
+                s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
+    const float tr = s00 + s11 + s22;
+    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, La - Lb, om);
+    // dS = dSXX - M (c' c^T + c c'^T) ; dI = tr(dS) I3 - dS
+    const float d00 = tXX[0] - 2.f * M * cA2d.x * cA2.x;
+    const float d01 = tXX[1] - M * (cA2d.x * cA2.y + cA2.x * cA2d.y);
+    const float d02 = tXX[2] - M * (cA2d.x * cA2.z + cA2.x * cA2d.z);
+    const float d11 = tXX[3] - 2.f * M * cA2d.y * cA2.y;
+    const float d12 = tXX[4] - M * (cA2d.y * cA2.z + cA2.y * cA2d.z);
+    const float d22 = tXX[5] - 2.f * M * cA2d.z * cA2.z;
+    const float dtr = d00 + d11 + d22;
+    const float3 dIom = make_float3((dtr - d00) * om.x - d01 * om.y - d02 * om.z,
+                                    -d01 * om.x + (dtr - d11) * om.y - d12 * om.z,
+                                    -d02 * om.x - d12 * om.y + (dtr - d22) * om.z);
+    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, (Lad - Lbd) - dIom, omd);
+  }
+
+  // (3) corrections and their tangents
+  bool bad = false;
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xa4 = a.Xout[p], va4 = a.Vout[p];
+    const float3 xad = f3(t.Xdout[p]), vad = f3(t.Vdout[p]);
+    const float3 r = (f3(xa4) - anc) - cA2;
+    const float3 rd = xad - cA2d;
+    const float3 corr = dv - cross(om, r);
+    const float3 corrd = dvd - cross(omd, r) - cross(om, rd);
+    const float3 v = f3(va4) + corr;
+    const float3 x = f3(xa4) + dt * corr;
+    const float3 vd = vad + corrd;
+    const float3 xd = xad + dt * corrd;
+    a.Xout[p] = make_float4(x.x, x.y, x.z, xa4.w);
+    a.Vout[p] = make_float4(v.x, v.y, v.z, 0.f);
+    t.Xdout[p] = make_float4(xd.x, xd.y, xd.z, 0.f);
+    t.Vdout[p] = make_float4(vd.x, vd.y, vd.z, 0.f);
+    bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(xd.x) && isfinite(xd.y) &&
+             isfinite(xd.z));
+  }
+  if (lane == 0) {
+    a.quat[b] = qrot;
+    const float3 cn = anc + cA2 + dt * dv;
+    a.bcom[b] = make_float4(cn.x, cn.y, cn.z, 0.f);
+  }
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(&a.scene_err[br.scene], (uint32_t)PBDR_EBIT_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
 // per-substep wrench accelerations: aF = F/M, alpha = I^-1 tau with c and I
 // of the current positions (one body per warp, anchored FP32 sums)
 // ---------------------------------------------------------------------------
@@ -494,6 +791,18 @@ int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s) {
   if (a.nbodies <= 0) return 0;
   (void)warps_per_block;
   k_iterate<<<blocks_for(a.nbodies, 4), 128, 0, s>>>(a);
+  return 1;
+}
+
+int launch_iterate_tangent(const IterArgs &a, const TangentArgs &t, cudaStream_t s) {
+  if (a.nbodies <= 0) return 0;
+  k_iterate_tangent<<<blocks_for(a.nbodies, 4), 128, 0, s>>>(a, t);
+  return 1;
+}
+
+int launch_predict_tangent(const TangentPredictArgs &a, cudaStream_t s) {
+  if (a.np <= 0) return 0;
+  k_predict_tangent<<<blocks_for(a.np, 256), 256, 0, s>>>(a);
   return 1;
 }
 
