@@ -70,6 +70,60 @@ __device__ __forceinline__ float wsum(float v) {
   return v;
 }
 
+// One step of a recursive-halving warp reduction of N values per lane over
+// lane distance D: lanes with bit D clear keep values [0, H), lanes with it
+// set keep [H, 2H) (indices >= N are zero), each adding its partner's copy.
+// With N = 1 both partners keep the single value.
+template <int N, int H, int D>
+__device__ __forceinline__ void halve(float *v, int lane) {
+  if (N == 1) {
+    v[0] += __shfl_xor_sync(kFull, v[0], D);
+    return;
+  }
+  const bool up = (lane & D) != 0;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float lo = v[k];
+    const float hi = (k + H < N) ? v[k + H] : 0.f;
+    v[k] = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, D);
+  }
+}
+
+// index of the value whose total lane `lane` holds after warp_sums<V>, or -1
+__host__ __device__ constexpr int ws_index(int V, int lane) {
+  const int N0 = V, N1 = (N0 + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2, N4 = (N3 + 1) / 2,
+            N5 = (N4 + 1) / 2;
+  const int o4 = (N4 > 1 && (lane & 1)) ? N5 : 0, o3 = (N3 > 1 && (lane & 2)) ? N4 : 0,
+            o2 = (N2 > 1 && (lane & 4)) ? N3 : 0, o1 = (N1 > 1 && (lane & 8)) ? N2 : 0,
+            o0 = (N0 > 1 && (lane & 16)) ? N1 : 0;
+  const int s4 = o4, s3 = s4 + o3, s2 = s3 + o2, s1 = s2 + o1, s0 = s1 + o0;
+  return (s4 < N4 && s3 < N3 && s2 < N2 && s1 < N1 && s0 < N0) ? s0 : -1;
+}
+
+// a lane holding the total of value j after warp_sums<V>
+__host__ __device__ constexpr int ws_lane(int V, int j) {
+  int found = 0;
+  for (int l = 31; l >= 0; --l)
+    if (ws_index(V, l) == j) found = l;
+  return found;
+}
+
+// Sums of V <= 32 values over the 32 lanes of a warp by recursive halving
+// (about V shuffles instead of 5 V for one butterfly per value): afterwards
+// lane l holds the total of value ws_index(V, l) in v[0].  The order of the
+// additions is fixed, so the sums are deterministic.
+template <int V>
+__device__ __forceinline__ void warp_sums(float *v, int lane) {
+  static_assert(V >= 1 && V <= 32, "one value per lane at most");
+  constexpr int N0 = V, N1 = (N0 + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2, N4 = (N3 + 1) / 2,
+                N5 = (N4 + 1) / 2;
+  halve<N0, N1, 16>(v, lane);
+  halve<N1, N2, 8>(v, lane);
+  halve<N2, N3, 4>(v, lane);
+  halve<N3, N4, 2>(v, lane);
+  halve<N4, N5, 1>(v, lane);
+}
+
 __device__ __forceinline__ void quat_mat(float4 q, float *R) {
   const float x = q.x, y = q.y, z = q.z, w = q.w;
   R[0] = 1.f - 2.f * (y * y + z * z);
@@ -501,13 +555,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           const float3 l = cross3(me, vb);
           red[15] += l.x; red[16] += l.y; red[17] += l.z;
         }
-#pragma unroll
-        for (int k = 0; k < 18; ++k) red[k] = wsum(red[k]);
-        if (lane == 0) {
+        warp_sums<18>(red, lane);
+        {
+          const int k = ws_index(18, lane);
           float *pt = part_local ? part_sm + kPartialFloats * (br.slot0 - slot_base + C.k)
                                  : a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
-#pragma unroll
-          for (int k = 0; k < 18; ++k) pt[k] = red[k];
+          if (k >= 0) pt[k] = red[0];
         }
       }
       __syncthreads();   // every contact of this iteration has read X_i
@@ -582,8 +635,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           red[9] += me.x * e.x; red[10] += me.x * e.y; red[11] += me.x * e.z;
           red[12] += me.y * e.y; red[13] += me.y * e.z; red[14] += me.z * e.z;
         }
+        warp_sums<15>(red, lane);
+        {
+          const float t0 = red[0];
 #pragma unroll
-        for (int k = 0; k < 15; ++k) red[k] = wsum(red[k]);
+          for (int k = 0; k < 15; ++k) red[k] = __shfl_sync(kFull, t0, ws_lane(15, k));
+        }
         // momentum enforcement (Sec. III-C)
         const float3 cA2 = mul(iM, make_float3(red[0], red[1], red[2]));
         const float3 Pa = make_float3(red[3], red[4], red[5]);
