@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch shapes instead of tuned ones")
     ap.add_argument("--grad-steps", type=int, default=200,
                     help="substeps of the differentiated 16-body run (0: skip)")
     ap.add_argument("--settle", type=int, default=240,
@@ -234,6 +236,9 @@ def run_pbdr(args, rank, world, local_rank):
 
     scs = make_workload(args, args.seed + rank)     # weak scaling: own batch per rank
     ctx = Context(local_rank)
+    if args.no_autotune:
+        from paper_2603_14634_gb300.binding import OPT_AUTOTUNE
+        ctx.set_option(OPT_AUTOTUNE, 0)
     ids = [ctx.create_scene(s) for s in scs]
     plan_cfg = None
     n_particles = sum(s.num_particles for s in scs)

@@ -125,7 +125,7 @@ __device__ bool polar_higham(const float *A, float *U) {
 // positive definite at the warm start (the start is far from the optimum),
 // the start is replaced by the polar factor from Higham's iteration; where
 // that fails too (singular or inverted A) damped gradient steps are taken.
-__device__ __noinline__ float4 shape_rotation(const float *A, float4 q) {
+__device__ __forceinline__ float4 shape_rotation(const float *A, float4 q) {
   bool restarted = false;
   for (int it = 0; it < 8; ++it) {
     float R[9];
