@@ -401,6 +401,19 @@ int fill_stream_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P, std
   return PBDR_OK;
 }
 
+// default launch shape of size class k: scratch and velocities in shared
+// memory where they fit, the class's thread count, every CTA the SMs hold
+int default_shape(pbdr_ctx *c, int k, Plan::FClass &F) {
+  F.ncap = kClassCaps[k];
+  F.dx_shared = fused_layout(F.ncap, true, false, true).bytes <= 220 * 1024;
+  F.v_shared = F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024;
+  F.threads = c->fused_threads ? c->fused_threads : kClassThreads[k];
+  const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.v_shared, F.threads);
+  if (per_sm < 1) return fail(PBDR_ERR_CUDA, "scene-resident kernel does not fit on an SM");
+  F.grid = std::min<int>(std::max(F.n, 1), per_sm * c->num_sms);
+  return PBDR_OK;
+}
+
 // scene-resident plan: scenes grouped by size class, the rest streamed
 int fill_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P) {
   P.ids.assign(ids, ids + n);
@@ -419,20 +432,15 @@ int fill_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P) {
   int rc;
   for (int k = 0; k < 4; ++k) {
     Plan::FClass &F = P.classes[k];
-    F.ncap = kClassCaps[k];
-    F.dx_shared = fused_layout(F.ncap, true, false, true).bytes <= 220 * 1024;
-    F.v_shared = F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024;
-    F.threads = c->fused_threads ? c->fused_threads : kClassThreads[k];
     F.n = (int32_t)F.ids.size();
+    F.ncap = kClassCaps[k];
     if (!F.n) continue;
     // largest scenes first: the persistent CTAs then finish together
     std::stable_sort(F.ids.begin(), F.ids.end(),
                      [&](int32_t a, int32_t b) { return c->sh[a].np > c->sh[b].np; });
     F.o_list = (int32_t)P.tab.size();
     P.tab.insert(P.tab.end(), F.ids.begin(), F.ids.end());
-    const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.v_shared, F.threads);
-    if (per_sm < 1) return fail(PBDR_ERR_CUDA, "scene-resident kernel does not fit on an SM");
-    F.grid = std::min<int>(F.n, per_sm * c->num_sms);
+    if ((rc = default_shape(c, k, F))) return rc;
     if (!F.dx_shared && !c->dx_scratch.p) {
       if ((rc = dev_alloc(c, c->dx_scratch, (size_t)c->pcap * sizeof(float4)))) return rc;
     }
@@ -865,9 +873,16 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
     if (P.classes[k].n) work.push_back({-w, k});
   }
   std::sort(work.begin(), work.end());
+  std::vector<int> todo;
   for (auto &wk : work) {
-    Plan::FClass &F = P.classes[wk.second];
-    if (F.n < c->num_sms || c->tune_memo.count({wk.second, F.n})) continue;
+    const Plan::FClass &F = P.classes[wk.second];
+    if (F.n >= c->num_sms && !c->tune_memo.count({wk.second, F.n})) todo.push_back(wk.second);
+  }
+  // two coordinate-descent passes: the second revisits every class with the
+  // others at their tuned shapes
+  for (int pass = 0; pass < 2; ++pass)
+  for (int kc : todo) {
+    Plan::FClass &F = P.classes[kc];
     struct Cand {
       float ms;
       int threads, grid;
@@ -914,9 +929,35 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
       }
     std::sort(cands.begin(), cands.begin() + top, [](const Cand &x, const Cand &y) { return x.ms < y.ms; });
     apply(cands[0]);
-    const int bt = F.threads, bg = F.grid;
-    const bool bd = F.dx_shared, bv = F.v_shared;
-    c->tune_memo[{wk.second, F.n}] = {bt, bd ? 1 : 0, bv ? 1 : 0, bg};
+  }
+  // guard: keep the tuned shapes only if whole substeps beat the defaults
+  if (!todo.empty()) {
+    std::array<Plan::FClass, 4> tuned_shapes = P.classes, defaults = P.classes;
+    for (int kc : todo)
+      if ((rc = default_shape(c, kc, defaults[kc]))) return rc;
+    auto set_shapes = [&](const std::array<Plan::FClass, 4> &src) {
+      for (int kc : todo) {
+        P.classes[kc].threads = src[kc].threads;
+        P.classes[kc].grid = src[kc].grid;
+        P.classes[kc].dx_shared = src[kc].dx_shared;
+        P.classes[kc].v_shared = src[kc].v_shared;
+      }
+    };
+    float t_tuned = 1e30f, t_default = 1e30f;
+    for (int round = 0; round < 3; ++round) {
+      float ms = 0.f;
+      set_shapes(tuned_shapes);
+      if ((rc = time_substeps(&ms))) return rc;
+      t_tuned = std::min(t_tuned, ms);
+      set_shapes(defaults);
+      if ((rc = time_substeps(&ms))) return rc;
+      t_default = std::min(t_default, ms);
+    }
+    set_shapes(t_tuned <= t_default ? tuned_shapes : defaults);
+    for (int kc : todo) {
+      const Plan::FClass &F = P.classes[kc];
+      c->tune_memo[{kc, F.n}] = {F.threads, F.dx_shared ? 1 : 0, F.v_shared ? 1 : 0, F.grid};
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
