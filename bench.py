@@ -469,19 +469,25 @@ def run_gradient(args, local_rank):
     sc = diff.c5_scene(seed=args.seed)
     v = np.stack([sc.vel[s].astype(np.float64).mean(0) for s in diff.body_slices(sc)])
     w = np.zeros_like(v)
+    wts = np.ones((sc.num_bodies, 3))
     with Context(local_rank) as c:
         diff.final_com_and_jacobian(c, sc, v, w, 3)        # warm: build, allocate
+        diff.com_gradient_reverse(c, sc, v, w, 3, wts)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, J = diff.final_com_and_jacobian(c, sc, v, w, args.grad_steps)
         secs = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        diff.com_gradient_reverse(c, sc, v, w, args.grad_steps, wts, checkpoint_every=20)
+        secs_rev = time.perf_counter() - t0
     dirs = J.shape[1]
     return {
-        "what": "d(final body CoMs)/d(initial v_b, omega_b), 16 bodies of 5^3, forward-mode tangents, all directions batched",
+        "what": "d(final body CoMs)/d(initial v_b, omega_b), 16 bodies of 5^3: full Jacobian by forward-mode tangents (all directions batched), and one gradient by the reverse-mode adjoint (checkpoints every 20 substeps)",
         "outputs": int(J.shape[0]), "directions": int(dirs), "substeps": args.grad_steps,
-        "ms": round(secs * 1e3, 2),
+        "jacobian_ms": round(secs * 1e3, 2),
         "tangent_particle_iters_per_s": round(dirs * sc.num_particles * sc.iterations * args.grad_steps / secs, 1),
-        "timing": "wall clock around the whole call (scene copies, seeds, tangent steps, read-back)",
+        "adjoint_gradient_ms": round(secs_rev * 1e3, 2),
+        "timing": "wall clock around each whole call (scene setup, seeds, steps, read-back)",
     }
 
 

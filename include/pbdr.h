@@ -228,6 +228,35 @@ int pbdr_write_tangent(pbdr_ctx *ctx, pbdr_scene scene, const float *dpos, const
  * synchronises `stream`.  PBDR_ERR_INVALID before any tangent exists. */
 int pbdr_read_tangent(pbdr_ctx *ctx, pbdr_scene scene, float *dpos, float *dvel, void *stream);
 
+/* Reverse mode (adjoint): the gradient of a scalar loss of the final state
+ * with respect to the initial state, through `substeps` substeps of the
+ * streaming form.  Before the call the adjoint buffers hold dLoss/dX, dLoss/dV
+ * of the final state (pbdr_write_adjoint); the scenes hold the initial state.
+ * The call runs the substeps forward, keeping device checkpoints every
+ * `checkpoint_every` substeps, then sweeps backward: each segment is run
+ * forward again from its checkpoint, and each substep once more keeping the
+ * state before each solver iteration, whose adjoint is then taken by hand-
+ * written kernels (the transpose of the derivative pbdr_step_tangent
+ * propagates: contacts with friction, shape matching and the rotation from
+ * the polar decomposition, velocity update, momentum constraint).  Contact
+ * terms are gathered per particle over the symmetric neighbour lists (no
+ * atomics: the result is deterministic).  On return the adjoint buffers hold
+ * dLoss/dX, dLoss/dV of the initial state (pbdr_read_adjoint) and the scenes
+ * hold the final state.  Device memory: (substeps/checkpoint_every +
+ * checkpoint_every + K + 1) saved states of the context (32 B per particle,
+ * 32 B per body each).  Same restrictions and errors as pbdr_step_tangent. */
+int pbdr_adjoint(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int32_t substeps,
+                 int32_t checkpoint_every, void *stream);
+
+/* Sets the adjoint (dLoss/dX, dLoss/dV, host [N*3], NULL = zero) of one
+ * scene's state; stream-ordered like pbdr_write_tangent. */
+int pbdr_write_adjoint(pbdr_ctx *ctx, pbdr_scene scene, const float *xbar, const float *vbar,
+                       void *stream);
+
+/* Reads one scene's adjoint into host [N*3] arrays (NULL = skip) and
+ * synchronises `stream`.  PBDR_ERR_INVALID before any adjoint exists. */
+int pbdr_read_adjoint(pbdr_ctx *ctx, pbdr_scene scene, float *xbar, float *vbar, void *stream);
+
 /* Launch shapes of the scene-resident kernel for the scene set ids[0..n):
  * out[5k..5k+4] = {particle capacity, scenes, threads per CTA, scratch bits
  * (1: velocities in shared memory, 2: per-particle scratch in shared memory),

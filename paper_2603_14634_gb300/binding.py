@@ -32,6 +32,7 @@ EXPORTS = [
     "pbdr_neighbor_total", "pbdr_set_profiling", "pbdr_read_profile",
     "pbdr_neighbors_noalloc", "pbdr_set_option", "pbdr_plan_config",
     "pbdr_step_tangent", "pbdr_write_tangent", "pbdr_read_tangent",
+    "pbdr_adjoint", "pbdr_write_adjoint", "pbdr_read_adjoint",
 ]
 NUM_STAGES = 6
 STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate", "scene_resident")
@@ -91,6 +92,9 @@ def load(path: Optional[str] = None):
     L.pbdr_step_tangent.argtypes = [vp, P(i32), i32, i32, vp]
     L.pbdr_write_tangent.argtypes = [vp, i32, vp, vp, vp]
     L.pbdr_read_tangent.argtypes = [vp, i32, vp, vp, vp]
+    L.pbdr_adjoint.argtypes = [vp, P(i32), i32, i32, i32, vp]
+    L.pbdr_write_adjoint.argtypes = [vp, i32, vp, vp, vp]
+    L.pbdr_read_adjoint.argtypes = [vp, i32, vp, vp, vp]
     L.pbdr_scene_info.argtypes = [vp, i32, P(i32), P(i32)]
     L.pbdr_last_error.argtypes = []
     L.pbdr_last_error.restype = C.c_char_p
@@ -214,6 +218,27 @@ def pbdr_read_tangent(ctx: int, scene: int, stream=None):
     dvel = np.empty((n, 3), np.float32)
     _check(load().pbdr_read_tangent(ctx, scene, _ptr(dpos), _ptr(dvel), _stream(stream)))
     return dpos, dvel
+
+
+def pbdr_adjoint(ctx: int, ids: Sequence[int], substeps: int, checkpoint_every: int = 20,
+                 stream=None) -> None:
+    arr, p = _ids(ids)
+    _check(load().pbdr_adjoint(ctx, p, len(arr), substeps, checkpoint_every, _stream(stream)))
+
+
+def pbdr_write_adjoint(ctx: int, scene: int, xbar=None, vbar=None, stream=None) -> None:
+    xbar = None if xbar is None else np.ascontiguousarray(xbar, dtype=np.float32)
+    vbar = None if vbar is None else np.ascontiguousarray(vbar, dtype=np.float32)
+    _check(load().pbdr_write_adjoint(ctx, scene, _ptr(xbar), _ptr(vbar), _stream(stream)))
+
+
+def pbdr_read_adjoint(ctx: int, scene: int, stream=None):
+    """-> (xbar [N,3], vbar [N,3])"""
+    n, _ = pbdr_scene_info(ctx, scene)
+    xb = np.empty((n, 3), np.float32)
+    vb = np.empty((n, 3), np.float32)
+    _check(load().pbdr_read_adjoint(ctx, scene, _ptr(xb), _ptr(vb), _stream(stream)))
+    return xb, vb
 
 
 def pbdr_scene_info(ctx: int, scene: int):
@@ -382,6 +407,17 @@ class Context:
 
     def read_tangent(self, sid: int, stream=None):
         return pbdr_read_tangent(self.h, sid, stream)
+
+    def adjoint(self, ids, substeps: int, checkpoint_every: int = 20, stream=None):
+        if isinstance(ids, (int, np.integer)):
+            ids = [int(ids)]
+        pbdr_adjoint(self.h, ids, substeps, checkpoint_every, stream)
+
+    def write_adjoint(self, sid: int, xbar=None, vbar=None, stream=None):
+        pbdr_write_adjoint(self.h, sid, xbar, vbar, stream)
+
+    def read_adjoint(self, sid: int, stream=None):
+        return pbdr_read_adjoint(self.h, sid, stream)
 
     def build_neighbors(self, ids, stream=None):
         if isinstance(ids, (int, np.integer)):

@@ -176,6 +176,8 @@ struct pbdr_ctx {
   int nbr_cap = 32;
   DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
   DevBuf Xd[2], Vd[2];             // tangents of X, V (forward-mode derivative), lazily allocated
+  DevBuf Xb[2], Vb[2], Ub;         // adjoints of X, V and of the contact corrections (reverse mode)
+  DevBuf adj_store;                // saved states of the reverse sweep
   DevBuf bodies, wrench, quat, bcom, biter, border;
   DevBuf dx_scratch, tickets, chunks, partials;
   int32_t ccap = 0, nc_used = 0;   // chunk (and partial-slot) capacity / use
@@ -762,6 +764,132 @@ int tangent_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   return PBDR_OK;
 }
 
+// adjoint buffers sized to the particle capacity; new space is zero
+int ensure_adjoint(pbdr_ctx *c) {
+  const size_t bytes = (size_t)std::max(c->pcap, 1) * sizeof(float4);
+  for (DevBuf *b : {&c->Xb[0], &c->Xb[1], &c->Vb[0], &c->Vb[1], &c->Ub}) {
+    if (b->bytes >= bytes) continue;
+    const size_t old = b->p ? std::min(b->bytes, (size_t)c->np_used * sizeof(float4)) : 0;
+    int rc = dev_grow(c, *b, bytes, old);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemset(b->as<unsigned char>() + old, 0, bytes - old));
+  }
+  return PBDR_OK;
+}
+
+// a saved state of the context: X, V of every particle, rotation warm start
+// and sum anchor of every body
+struct StateSlots {
+  float4 *base = nullptr;
+  size_t np = 0, nb = 0;
+  float4 *slot(int k) const { return base + (size_t)k * (2 * np + 2 * nb); }
+};
+
+int save_state(pbdr_ctx *c, const StateSlots &S, int k, cudaStream_t s) {
+  float4 *d = S.slot(k);
+  CUDA_TRY(cudaMemcpyAsync(d, c->X[0].p, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d + S.np, c->V[0].p, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d + 2 * S.np, c->quat.p, S.nb * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d + 2 * S.np + S.nb, c->bcom.p, S.nb * 16, cudaMemcpyDeviceToDevice, s));
+  return PBDR_OK;
+}
+
+int load_state(pbdr_ctx *c, const StateSlots &S, int k, cudaStream_t s) {
+  const float4 *d = S.slot(k);
+  CUDA_TRY(cudaMemcpyAsync(c->X[0].p, d, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->V[0].p, d + S.np, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->quat.p, d + 2 * S.np, S.nb * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->bcom.p, d + 2 * S.np + S.nb, S.nb * 16, cudaMemcpyDeviceToDevice, s));
+  return PBDR_OK;
+}
+
+// Reverse of one substep of a streaming plan, from the saved state at its
+// start (loaded into X[0], V[0], quat, bcom) and the adjoint of its end state
+// in Xb[0], Vb[0]; leaves the adjoint of its start state in Xb[0], Vb[0].
+// The substep is run forward again, keeping the state before every
+// iteration in slots it0 .. it0 + K - 1 of S.
+int adjoint_substep(pbdr_ctx *c, Plan &P, const StateSlots &S, int it0, cudaStream_t s, int64_t &launches) {
+  if (P.np == 0) return PBDR_OK;
+  const int K = P.kmax;
+  float4 *X0 = c->X[0].as<float4>(), *V0 = c->V[0].as<float4>();
+  float4 *X1 = c->X[1].as<float4>(), *V1 = c->V[1].as<float4>();
+  const bool odd = K % 2 == 1;
+  float4 *Xp = odd ? X1 : X0, *Vp = odd ? V1 : V0;
+  launches += launch_predict(predict_args(c, P, X0, V0, Xp, Vp, 1), s);
+  int rc = neighbor_stage(c, P, Xp, s, launches);
+  if (rc) return rc;
+  IterArgs ia{};
+  ia.Q = c->Q.as<float4>();
+  ia.Xinit = nullptr;
+  ia.nbr_cnt = c->nbr_cnt.as<int32_t>();
+  ia.nbr = c->nbr.as<int32_t>();
+  ia.nbr_stride = c->pcap;
+  ia.bodies = c->bodies.as<BodyRec>();
+  ia.scenes = c->scenes.as<ScenePar>();
+  ia.bmap = P.bcontig ? nullptr : c->s_bmap.as<int32_t>();
+  ia.bbase = P.bbase;
+  ia.nbodies = P.nb;
+  ia.scene_err = c->scene_err.as<uint32_t>();
+  // forward, keeping the state before every iteration
+  for (int k = 0; k < K; ++k) {
+    const int out = (K - 1 - k) % 2;
+    float4 *xin = out ? X0 : X1, *vin = out ? V0 : V1;
+    float4 *d = S.slot(it0 + k);
+    CUDA_TRY(cudaMemcpyAsync(d, xin, S.np * 16, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d + S.np, vin, S.np * 16, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d + 2 * S.np, c->quat.p, S.nb * 16, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d + 2 * S.np + S.nb, c->bcom.p, S.nb * 16, cudaMemcpyDeviceToDevice, s));
+    ia.Xin = xin;
+    ia.Vin = vin;
+    ia.Xout = out ? X1 : X0;
+    ia.Vout = out ? V1 : V0;
+    ia.quat = c->quat.as<float4>();
+    ia.bcom = c->bcom.as<float4>();
+    ia.k = k;
+    launches += launch_iterate(ia, 4, s);
+  }
+  // backward through the iterations; Xb/Vb ping-pong, ending in buffer `cur`
+  int cur = 0;
+  const int32_t *pmap = P.pcontig ? nullptr : c->s_pmap.as<int32_t>();
+  for (int k = K - 1; k >= 0; --k) {
+    float4 *d = S.slot(it0 + k);
+    ia.Xin = d;
+    ia.Vin = d + S.np;
+    ia.quat = d + 2 * S.np;
+    ia.bcom = d + 2 * S.np + S.nb;
+    ia.Xout = X1;   // scratch for X_bsm, V_bsm
+    ia.Vout = V1;
+    ia.k = k;
+    AdjointArgs ta{};
+    ta.Xbin = c->Xb[cur].as<float4>();
+    ta.Vbin = c->Vb[cur].as<float4>();
+    ta.Xbout = c->Xb[1 - cur].as<float4>();
+    ta.Vbout = c->Vb[1 - cur].as<float4>();
+    ta.U = c->Ub.as<float4>();
+    launches += launch_iterate_adjoint(ia, ta, c->pbody.as<int32_t>(), pmap, P.pbase, P.np, s);
+    cur = 1 - cur;
+  }
+  TangentPredictArgs tp{};
+  tp.Xd0 = c->Xb[cur].as<float4>();
+  tp.Vd0 = c->Vb[cur].as<float4>();
+  tp.Xdp = c->Xb[1 - cur].as<float4>();
+  tp.Vdp = c->Vb[1 - cur].as<float4>();
+  tp.pbody = c->pbody.as<int32_t>();
+  tp.bodies = c->bodies.as<BodyRec>();
+  tp.scenes = c->scenes.as<ScenePar>();
+  tp.pmap = pmap;
+  tp.pbase = P.pbase;
+  tp.np = P.np;
+  launches += launch_predict_adjoint(tp, s);
+  cur = 1 - cur;
+  if (cur != 0) {   // both buffers agree outside the plan's particles
+    CUDA_TRY(cudaMemcpyAsync(c->Xb[0].p, c->Xb[1].p, S.np * 16, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Vb[0].p, c->Vb[1].p, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaGetLastError());
+  return PBDR_OK;
+}
+
 int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   int rc = ensure_class_streams(c);
   if (rc) return rc;
@@ -1058,7 +1186,7 @@ __global__ void k_errs(uint32_t *scene_err, const int32_t *ids, int32_t n, uint3
 // gather / scatter of xyz state for scenes ids[0..n) through device staging
 int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, float *hvel,
                     const float *cpos, const float *cvel, uint32_t *err_bits, int unpack,
-                    cudaStream_t s, bool tangent = false) {
+                    cudaStream_t s, float4 *bufX = nullptr, float4 *bufV = nullptr) {
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
   std::vector<int32_t> p0(n);
@@ -1080,8 +1208,8 @@ int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, 
   CUDA_TRY(cudaMemcpyAsync(c->seg_p0.p, p0.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(c->seg_off.p, off.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
   PackArgs pa{};
-  pa.X = tangent ? c->Xd[0].as<float4>() : c->X[0].as<float4>();
-  pa.V = tangent ? c->Vd[0].as<float4>() : c->V[0].as<float4>();
+  pa.X = bufX ? bufX : c->X[0].as<float4>();
+  pa.V = bufV ? bufV : c->V[0].as<float4>();
   pa.hpos = want_pos ? c->stage_pos.as<float>() : nullptr;
   pa.hvel = want_vel ? c->stage_vel.as<float>() : nullptr;
   pa.seg_p0 = c->seg_p0.as<int32_t>();
@@ -1336,6 +1464,11 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   }
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
+  if (c->Xb[0].p && N > 0) {   // adjoints in use: the new scene starts with zero adjoints
+    if ((rc = ensure_adjoint(c))) return rc;
+    for (DevBuf *b : {&c->Xb[0], &c->Xb[1], &c->Vb[0], &c->Vb[1], &c->Ub})
+      CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
+  }
   if (c->Xd[0].p && N > 0) {   // tangents in use: the new scene starts with zero tangents
     if ((rc = ensure_tangent(c))) return rc;
     for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]})
@@ -1512,7 +1645,8 @@ int pbdr_write_tangent(pbdr_ctx *c, pbdr_scene s, const float *dpos, const float
   for (DevBuf *b : {&c->Xd[0], &c->Vd[0]})
     CUDA_TRY(cudaMemsetAsync(b->as<float4>() + S.p0, 0, (size_t)S.np * sizeof(float4), st));
   if (!dpos && !dvel) return PBDR_OK;
-  return transfer_states(c, &s, 1, nullptr, nullptr, dpos, dvel, nullptr, 1, st, true);
+  return transfer_states(c, &s, 1, nullptr, nullptr, dpos, dvel, nullptr, 1, st, c->Xd[0].as<float4>(),
+                         c->Vd[0].as<float4>());
 }
 
 int pbdr_read_tangent(pbdr_ctx *c, pbdr_scene s, float *dpos, float *dvel, void *stream) {
@@ -1521,7 +1655,88 @@ int pbdr_read_tangent(pbdr_ctx *c, pbdr_scene s, float *dpos, float *dvel, void 
   if (rc) return rc;
   if (!c->Xd[0].p) return fail(PBDR_ERR_INVALID, "no tangent has been written");
   if (c->sh[s].np == 0) return PBDR_OK;
-  return transfer_states(c, &s, 1, dpos, dvel, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream, true);
+  return transfer_states(c, &s, 1, dpos, dvel, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream,
+                         c->Xd[0].as<float4>(), c->Vd[0].as<float4>());
+}
+
+int pbdr_adjoint(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, int32_t checkpoint_every,
+                 void *stream) {
+  g_err.clear();
+  if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
+  if (substeps < 0) return fail(PBDR_ERR_INVALID, "substeps must be >= 0");
+  if (checkpoint_every < 1) return fail(PBDR_ERR_INVALID, "checkpoint_every must be >= 1");
+  int rc = check_ids(c, ids, n);
+  if (rc) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    const SceneHost &S = c->sh[ids[i]];
+    if (S.wrench_bodies) return fail(PBDR_ERR_UNSUPPORTED, "adjoint substeps of scenes with a body wrench");
+    if (S.par.flags & (kStdVelocity | PBDR_SM_FROM_XI))
+      return fail(PBDR_ERR_UNSUPPORTED, "adjoint substeps with PBDR_STD_VELOCITY or PBDR_SM_FROM_XI");
+  }
+  Plan *P = nullptr;
+  if ((rc = build_plan(c, ids, n, &P, 1))) return rc;
+  if ((rc = ensure_adjoint(c))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = activate(c, P, s))) return rc;
+  if (substeps == 0) return PBDR_OK;
+  const int T = substeps, C = std::min(checkpoint_every, substeps);
+  const int nck = (T + C - 1) / C, K = std::max(P->kmax, 1);
+  StateSlots S;
+  S.np = (size_t)std::max(c->np_used, 1);
+  S.nb = (size_t)std::max(c->nb_used, 1);
+  const int slots = nck + C + K + 1;   // checkpoints | segment | iterations | final
+  if ((rc = dev_alloc(c, c->adj_store, (size_t)slots * (2 * S.np + 2 * S.nb) * sizeof(float4)))) return rc;
+  S.base = c->adj_store.as<float4>();
+  const int seg0 = nck, it0 = nck + C, fin = nck + C + K;
+  int64_t launches = 0;
+  for (int t = 0; t < T; ++t) {   // forward, with checkpoints
+    if (t % C == 0 && (rc = save_state(c, S, t / C, s))) return rc;
+    if ((rc = substep(c, *P, s, launches))) return rc;
+  }
+  if ((rc = save_state(c, S, fin, s))) return rc;
+  CUDA_TRY(cudaMemcpyAsync(c->Xb[1].p, c->Xb[0].p, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->Vb[1].p, c->Vb[0].p, S.np * 16, cudaMemcpyDeviceToDevice, s));
+  for (int sg = nck - 1; sg >= 0; --sg) {   // reverse, one segment at a time
+    const int t0 = sg * C, t1 = std::min(T, t0 + C);
+    if ((rc = load_state(c, S, sg, s))) return rc;
+    for (int t = t0; t < t1; ++t) {
+      if ((rc = save_state(c, S, seg0 + (t - t0), s))) return rc;
+      if (t + 1 < t1 && (rc = substep(c, *P, s, launches))) return rc;
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      if ((rc = load_state(c, S, seg0 + (t - t0), s))) return rc;
+      if ((rc = adjoint_substep(c, *P, S, it0, s, launches))) return rc;
+    }
+  }
+  if ((rc = load_state(c, S, fin, s))) return rc;
+  c->last_launches = launches;
+  c->last_nbr_plan = nullptr;   // the lists now belong to a recomputed substep
+  return PBDR_OK;
+}
+
+int pbdr_write_adjoint(pbdr_ctx *c, pbdr_scene s, const float *xbar, const float *vbar, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if ((rc = ensure_adjoint(c))) return rc;
+  const SceneHost &S = c->sh[s];
+  if (S.np == 0) return PBDR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (DevBuf *b : {&c->Xb[0], &c->Vb[0]})
+    CUDA_TRY(cudaMemsetAsync(b->as<float4>() + S.p0, 0, (size_t)S.np * sizeof(float4), st));
+  if (!xbar && !vbar) return PBDR_OK;
+  return transfer_states(c, &s, 1, nullptr, nullptr, xbar, vbar, nullptr, 1, st, c->Xb[0].as<float4>(),
+                         c->Vb[0].as<float4>());
+}
+
+int pbdr_read_adjoint(pbdr_ctx *c, pbdr_scene s, float *xbar, float *vbar, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (!c->Xb[0].p) return fail(PBDR_ERR_INVALID, "no adjoint has been written");
+  if (c->sh[s].np == 0) return PBDR_OK;
+  return transfer_states(c, &s, 1, xbar, vbar, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream,
+                         c->Xb[0].as<float4>(), c->Vb[0].as<float4>());
 }
 
 int pbdr_scene_info(pbdr_ctx *c, pbdr_scene s, int32_t *np, int32_t *nb) {

@@ -186,6 +186,17 @@ struct TangentPredictArgs {
   int32_t pbase, np;
 };
 
+// Adjoint (reverse-mode derivative) of one solver iteration of the streaming
+// form.  The primal inputs are the saved state at the start of the iteration
+// (IterArgs::Xin/Vin, quat and bcom as they were before it); Xout/Vout serve
+// as scratch for X_bsm, V_bsm.
+struct AdjointArgs {
+  const float4 *Xbin, *Vbin;   // adjoint of X_{i+1}, V_{i+1}
+  float4 *Xbout, *Vbout;       // adjoint of X_i, V_i
+  float4 *U;                   // per particle: adjoint of the contact correction dX (xyz),
+                               // the particle's contact weight (w)
+};
+
 struct WrenchArgs {
   const float4 *X, *Q;
   const BodyRec *bodies;
@@ -211,6 +222,9 @@ int launch_neighbors(const NbrArgs &a, cudaStream_t s);
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_iterate_tangent(const IterArgs &a, const TangentArgs &t, cudaStream_t s);
 int launch_predict_tangent(const TangentPredictArgs &a, cudaStream_t s);
+int launch_iterate_adjoint(const IterArgs &a, const AdjointArgs &t, const int32_t *pbody, const int32_t *pmap,
+                           int32_t pbase, int32_t np, cudaStream_t s);
+int launch_predict_adjoint(const TangentPredictArgs &a, cudaStream_t s);
 int launch_wrench(const WrenchArgs &a, cudaStream_t s);
 int launch_pack(const PackArgs &a, int unpack, cudaStream_t s);
 int launch_expand_map(const int32_t *seg_start, const int32_t *seg_base, int32_t nseg, int32_t *map,

@@ -675,6 +675,358 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint (reverse-mode derivative) of one solver iteration.
+//
+// k_iterate_adjoint_body (one body per warp) recomputes the iteration from
+// the saved state at its start (same arithmetic as k_iterate) and takes the
+// adjoint of X_{i+1}, V_{i+1} back through the momentum correction, the
+// velocity update and shape matching to X_bsm, V_bsm:
+//   corr = dv - w x r        ->  dv~ = sum c~,  w~ = -sum r x c~,  r~ = w x c~
+//   w = I^-1 (L_asm - L_bsm) ->  y = I^-1 w~,  L~_asm = y, L~_bsm = -y,
+//                                 I~ = -y w^T (through I = sum m (|r|^2 - r r^T))
+//   dv = (P_bsm - P_asm)/M   ->  P~_bsm = dv~/M, P~_asm = -dv~/M
+//   R = polar(A)             ->  A~ = R [z]x, (tr(S) I - S) z = axial(R^T R~ - R~^T R)
+// and leaves, per particle, the direct parts of the adjoints of X_i, V_i and
+// u = adjoint of the contact correction dX (X_bsm = X_i + dX, V_bsm = V_i + dX/dt).
+// k_contact_adjoint (one particle per thread) adds the contact terms: for a
+// pair term s_p T(x_p - x_q, v_p - v_q) of p and its mirror -s_q T(...) of q
+// (T is odd), particle p gathers J^T (s_p u_p - s_q u_q) over its own
+// (symmetric) list; no scatter, no atomics.  Jacobians of T and of the ground
+// term are built column by column from the tangent functions above.
+// ---------------------------------------------------------------------------
+
+// weight of a particle's pair terms: 1, or 1 / (active pairs) with PBDR_CONTACT_AVG
+__device__ __forceinline__ float contact_weight(const IterArgs &a, const ScenePar &sp, int32_t p, float4 xp) {
+  if (!(sp.flags & kContactAvg)) return 1.f;
+  const float d_c = 2.f * sp.radius;
+  const int32_t cnt = a.nbr_cnt[p];
+  int active = 0;
+  for (int32_t j = 0; j < cnt; ++j) {
+    const float3 diff = f3(xp) - f3(a.Xin[a.nbr[(int64_t)j * a.nbr_stride + p]]);
+    const float dd = dot(diff, diff);
+    active += (dd > 0.f && dd < d_c * d_c) ? 1 : 0;
+  }
+  return active > 0 ? 1.f / (float)active : 1.f;
+}
+
+__global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, AdjointArgs t) {
+  const int lane = threadIdx.x & 31;
+  const int32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.nbodies) return;
+  const int32_t b = a.bmap ? a.bmap[w] : a.bbase + w;
+  const BodyRec br = a.bodies[b];
+  const ScenePar sp = a.scenes[br.scene];
+  const int32_t p0 = br.start, pe = br.start + br.count;
+  if (a.k >= sp.iterations) {   // the iteration carried the state: the adjoint passes through
+    for (int32_t p = p0 + lane; p < pe; p += 32) {
+      t.Xbout[p] = t.Xbin[p];
+      t.Vbout[p] = t.Vbin[p];
+      t.U[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return;
+  }
+  const float dt = sp.dt, idt = sp.inv_dt;
+  const float3 anc = f3(a.bcom[b]);
+  const bool linm = !(sp.flags & kNoLinMom), angm = !(sp.flags & kNoAngMom);
+
+  // ---- forward recomputation (as k_iterate) ----
+  float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xp = a.Xin[p], vp = a.Vin[p];
+    const float3 dX = contact_dx(a, sp, p, xp, vp);
+    const float3 xb = f3(xp) + dX;
+    const float3 vb = f3(vp) + idt * dX;
+    a.Xout[p] = make_float4(xb.x, xb.y, xb.z, xp.w);
+    a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 e = xb - anc;
+    const float3 me = m * e;
+    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
+    sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
+    sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
+    sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
+    sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
+    const float3 l = cross(me, vb);
+    sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sx[k] = warp_sum(sx[k]);
+    sP[k] = warp_sum(sP[k]);
+    sL[k] = warp_sum(sL[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) sA[k] = warp_sum(sA[k]);
+  const float iM = br.inv_mass, M = br.mass;
+  const float3 cA = iM * make_float3(sx[0], sx[1], sx[2]);
+  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
+  float A[9];
+  {
+    const float qs[3] = {br.qsx, br.qsy, br.qsz};
+    const float ca[3] = {cA.x, cA.y, cA.z};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
+  }
+  const float4 qrot = shape_rotation(A, a.quat[b]);
+  float R[9];
+  quat_to_mat(qrot, R);
+  auto goal = [&](float4 q) {   // R q + c - anchor
+    return make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z, R[3] * q.x + R[4] * q.y + R[5] * q.z,
+                       R[6] * q.x + R[7] * q.y + R[8] * q.z) + cA;
+  };
+  float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f}, sXX[6] = {0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 grel = goal(q);
+    const float3 dsm = grel - (f3(xb4) - anc);
+    const float3 xa = f3(xb4) + dsm;
+    const float3 va = f3(vb4) + idt * dsm;
+    const float3 e = xa - anc;
+    const float3 me = m * e;
+    sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
+    sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
+    const float3 l = cross(me, va);
+    sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
+    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
+    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sx2[k] = warp_sum(sx2[k]);
+    sP2[k] = warp_sum(sP2[k]);
+    sL2[k] = warp_sum(sL2[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
+  const float3 cA2 = iM * make_float3(sx2[0], sx2[1], sx2[2]);
+  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
+  const float3 Lb = make_float3(sL[0], sL[1], sL[2]) - cross(cA, Pb);
+  const float3 La = make_float3(sL2[0], sL2[1], sL2[2]) - cross(cA2, Pa);
+  const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
+              s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
+              s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
+  const float trI = s00 + s11 + s22;
+  float3 om = make_float3(0.f, 0.f, 0.f);
+  if (angm) solve_sym3(trI - s00, -s01, -s02, trI - s11, -s12, trI - s22, La - Lb, om);
+
+  // ---- backward: corrections -> dv~, w~ ----
+  float sdv[3] = {0.f, 0.f, 0.f}, sw[3] = {0.f, 0.f, 0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p];
+    const float3 xa = f3(xb4) + (goal(a.Q[p]) - (f3(xb4) - anc));
+    const float3 r = (xa - anc) - cA2;
+    const float3 cb = f3(t.Vbin[p]) + dt * f3(t.Xbin[p]);
+    sdv[0] += cb.x; sdv[1] += cb.y; sdv[2] += cb.z;
+    const float3 rc = cross(r, cb);
+    sw[0] -= rc.x; sw[1] -= rc.y; sw[2] -= rc.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sdv[k] = warp_sum(sdv[k]);
+    sw[k] = warp_sum(sw[k]);
+  }
+  const float3 dvb = linm ? make_float3(sdv[0], sdv[1], sdv[2]) : make_float3(0.f, 0.f, 0.f);
+  float3 y = make_float3(0.f, 0.f, 0.f);
+  if (angm) solve_sym3(trI - s00, -s01, -s02, trI - s11, -s12, trI - s22, make_float3(sw[0], sw[1], sw[2]), y);
+  const float3 Lab = y, Lbb = make_float3(-y.x, -y.y, -y.z);
+  const float yw = dot(y, om);
+  // r~ of a particle (corrections, I, L_asm)
+  auto rbar = [&](float3 r, float3 cb, float3 va, float m) {
+    float3 rb = make_float3(0.f, 0.f, 0.f);
+    if (angm) {
+      rb = cross(om, cb) + m * ((-2.f * yw) * r + dot(om, r) * y + dot(y, r) * om) + m * cross(va, Lab);
+    }
+    return rb;
+  };
+  float srb[3] = {0.f, 0.f, 0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
+    const float4 q = a.Q[p];
+    const float3 dsm = goal(q) - (f3(xb4) - anc);
+    const float3 xa = f3(xb4) + dsm;
+    const float3 va = f3(vb4) + idt * dsm;
+    const float3 r = (xa - anc) - cA2;
+    const float3 cb = f3(t.Vbin[p]) + dt * f3(t.Xbin[p]);
+    const float3 rb = rbar(r, cb, va, q.w);
+    srb[0] += rb.x; srb[1] += rb.y; srb[2] += rb.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) srb[k] = warp_sum(srb[k]);
+  const float3 cab = make_float3(-srb[0], -srb[1], -srb[2]);   // adjoint of c_asm
+  // ---- backward: X_asm, V_asm -> goals -> R~, c~ ----
+  float sRb[9] = {0.f}, scg[3] = {0.f, 0.f, 0.f};
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 dsm = goal(q) - (f3(xb4) - anc);
+    const float3 xa = f3(xb4) + dsm;
+    const float3 va = f3(vb4) + idt * dsm;
+    const float3 r = (xa - anc) - cA2;
+    const float3 xp1 = f3(t.Xbin[p]), vp1 = f3(t.Vbin[p]);
+    const float3 cb = vp1 + dt * xp1;
+    const float3 xab = xp1 + rbar(r, cb, va, m) + (m * iM) * cab;
+    float3 vab = vp1 + (-m * iM) * dvb;
+    if (angm) vab = vab + m * cross(Lab, r);
+    const float3 gb = xab + idt * vab;
+    sRb[0] += gb.x * q.x; sRb[1] += gb.x * q.y; sRb[2] += gb.x * q.z;
+    sRb[3] += gb.y * q.x; sRb[4] += gb.y * q.y; sRb[5] += gb.y * q.z;
+    sRb[6] += gb.z * q.x; sRb[7] += gb.z * q.y; sRb[8] += gb.z * q.z;
+    scg[0] += gb.x; scg[1] += gb.y; scg[2] += gb.z;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) sRb[k] = warp_sum(sRb[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) scg[k] = warp_sum(scg[k]);
+  // A~ = R [z]x with (tr(S) I - S) z = axial(R^T R~ - R~^T R), S = R^T A
+  float Ab[9];
+  {
+    float S[9], Bm[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        S[3 * i + j] = R[i] * A[j] + R[3 + i] * A[3 + j] + R[6 + i] * A[6 + j];
+        Bm[3 * i + j] = R[i] * sRb[j] + R[3 + i] * sRb[3 + j] + R[6 + i] * sRb[6 + j];   // R^T R~
+      }
+    const float3 ax = make_float3(Bm[7] - Bm[5], Bm[2] - Bm[6], Bm[3] - Bm[1]);
+    const float t01 = 0.5f * (S[1] + S[3]), t02 = 0.5f * (S[2] + S[6]), t12 = 0.5f * (S[5] + S[7]);
+    const float tr = S[0] + S[4] + S[8];
+    float3 z;
+    solve_sym3(tr - S[0], -t01, -t02, tr - S[4], -t12, tr - S[8], ax, z);
+    // [z]x = [[0,-z3,z2],[z3,0,-z1],[-z2,z1,0]] ; A~ = R [z]x
+    const float Zx[9] = {0.f, -z.z, z.y, z.z, 0.f, -z.x, -z.y, z.x, 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Ab[3 * i + j] = R[3 * i] * Zx[j] + R[3 * i + 1] * Zx[3 + j] + R[3 * i + 2] * Zx[6 + j];
+  }
+  // adjoint of c: from the goals and from L_bsm (through e = x_bsm - c)
+  const float3 cb_tot = make_float3(scg[0], scg[1], scg[2]) - cross(Pb, Lbb);
+  // ---- backward: X_bsm, V_bsm -> u = adjoint of dX; direct adjoints of X_i, V_i ----
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
+    const float4 q = a.Q[p];
+    const float m = q.w;
+    const float3 dsm = goal(q) - (f3(xb4) - anc);
+    const float3 xa = f3(xb4) + dsm;
+    const float3 va = f3(vb4) + idt * dsm;
+    const float3 r = (xa - anc) - cA2;
+    const float3 xp1 = f3(t.Xbin[p]), vp1 = f3(t.Vbin[p]);
+    const float3 cb = vp1 + dt * xp1;
+    float3 vab = vp1 + (-m * iM) * dvb;
+    if (angm) vab = vab + m * cross(Lab, r);
+    const float3 e = (f3(xb4) - anc) - cA;
+    const float3 Aq = make_float3(Ab[0] * q.x + Ab[1] * q.y + Ab[2] * q.z, Ab[3] * q.x + Ab[4] * q.y + Ab[5] * q.z,
+                                  Ab[6] * q.x + Ab[7] * q.y + Ab[8] * q.z);
+    float3 xbb = (-idt) * vab + m * Aq + (m * iM) * cb_tot;
+    float3 vbb = vab + (m * iM) * dvb;
+    if (angm) {
+      xbb = xbb + m * cross(f3(vb4), Lbb);
+      vbb = vbb + m * cross(Lbb, e);
+    }
+    (void)cb;
+    t.Xbout[p] = make_float4(xbb.x, xbb.y, xbb.z, 0.f);
+    t.Vbout[p] = make_float4(vbb.x, vbb.y, vbb.z, 0.f);
+    const float3 u = xbb + idt * vbb;
+    t.U[p] = make_float4(u.x, u.y, u.z, contact_weight(a, sp, p, a.Xin[p]));
+  }
+}
+
+// columns of the Jacobian of a pair term T(d, w) = pen n - f(dt w, n, mu pen)
+// applied to a~: returns J_d^T a~ and J_w^T a~
+__device__ __forceinline__ void pair_vjp(float3 diff, float3 vrel, float dc, float mu, float dt, float3 ab,
+                                         float3 &gd, float3 &gw) {
+  const float3 zero = make_float3(0.f, 0.f, 0.f);
+  const float d = sqrtf(dot(diff, diff));
+  const float pen = dc - d;
+  const float3 nh = (1.f / d) * diff;
+  const float3 del = dt * vrel;
+  float out_d[3], out_w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float3 ek = make_float3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f);
+    const float d_d = dot(nh, ek);
+    const float3 nh_d = (1.f / d) * (ek - d_d * nh);
+    const float3 Td = (-d_d) * nh + pen * nh_d - friction_cut_d(del, zero, nh, nh_d, mu * pen, -mu * d_d);
+    const float3 Tw = zero - friction_cut_d(del, dt * ek, nh, zero, mu * pen, 0.f);
+    out_d[k] = dot(ab, Td);
+    out_w[k] = dot(ab, Tw);
+  }
+  gd = make_float3(out_d[0], out_d[1], out_d[2]);
+  gw = make_float3(out_w[0], out_w[1], out_w[2]);
+}
+
+__global__ void __launch_bounds__(256) k_contact_adjoint(IterArgs a, AdjointArgs t, const int32_t *pbody,
+                                                         const int32_t *pmap, int32_t pbase, int32_t np) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const int32_t p = pmap ? pmap[i] : pbase + i;
+  const ScenePar sp = a.scenes[a.bodies[pbody[p]].scene];
+  if (a.k >= sp.iterations) return;
+  const float r = sp.radius, d_c = 2.f * r, mu = sp.friction, dt = sp.dt;
+  const float3 n = make_float3(sp.nx, sp.ny, sp.nz);
+  const float3 zero = make_float3(0.f, 0.f, 0.f);
+  const float4 xp = a.Xin[p], vp = a.Vin[p];
+  const float4 up4 = t.U[p];
+  const float3 up = f3(up4);
+  float3 xb = f3(t.Xbout[p]), vb = f3(t.Vbout[p]);
+  // ground term: J^T u column by column
+  const float pen_g = r - (dot(n, f3(xp)) - sp.nd);
+  if (pen_g > 0.f) {
+    const float3 del = dt * f3(vp);
+    float gx[3], gv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float3 ek = make_float3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f);
+      const float pen_d = -dot(n, ek);
+      const float3 cx = pen_d * n - friction_cut_d(del, zero, n, zero, mu * pen_g, mu * pen_d);
+      const float3 cv = zero - friction_cut_d(del, dt * ek, n, zero, mu * pen_g, 0.f);
+      gx[k] = dot(up, cx);
+      gv[k] = dot(up, cv);
+    }
+    xb = xb + make_float3(gx[0], gx[1], gx[2]);
+    vb = vb + make_float3(gv[0], gv[1], gv[2]);
+  }
+  // pair terms over the symmetric list
+  const int32_t cnt = a.nbr_cnt[p];
+  for (int32_t j = 0; j < cnt; ++j) {
+    const int32_t q = a.nbr[(int64_t)j * a.nbr_stride + p];
+    const float4 xq = a.Xin[q];
+    const float3 diff = f3(xp) - f3(xq);
+    const float dd = dot(diff, diff);
+    if (!(dd > 0.f && dd < d_c * d_c)) continue;
+    const float4 uq4 = t.U[q];
+    const float sw = xp.w + xq.w;
+    const float3 ab = (xp.w / sw * up4.w) * up - (xq.w / sw * uq4.w) * f3(uq4);
+    float3 gd, gw;
+    pair_vjp(diff, f3(vp) - f3(a.Vin[q]), d_c, mu, dt, ab, gd, gw);
+    xb = xb + gd;
+    vb = vb + gw;
+  }
+  t.Xbout[p] = make_float4(xb.x, xb.y, xb.z, 0.f);
+  t.Vbout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
+}
+
+// adjoint of the prediction: x~ = x + dt v~, v~ = v + dt g
+__global__ void __launch_bounds__(256) k_predict_adjoint(TangentPredictArgs a) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
+  const ScenePar sp = a.scenes[a.bodies[a.pbody[p]].scene];
+  const float3 xb = f3(a.Xd0[p]);
+  const float3 vb = f3(a.Vd0[p]) + sp.dt * xb;
+  a.Xdp[p] = make_float4(xb.x, xb.y, xb.z, 0.f);
+  a.Vdp[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
+}
+
+// ---------------------------------------------------------------------------
 // per-substep wrench accelerations: aF = F/M, alpha = I^-1 tau with c and I
 // of the current positions (one body per warp, anchored FP32 sums)
 // ---------------------------------------------------------------------------
@@ -797,6 +1149,20 @@ int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s) {
 int launch_iterate_tangent(const IterArgs &a, const TangentArgs &t, cudaStream_t s) {
   if (a.nbodies <= 0) return 0;
   k_iterate_tangent<<<blocks_for(a.nbodies, 4), 128, 0, s>>>(a, t);
+  return 1;
+}
+
+int launch_iterate_adjoint(const IterArgs &a, const AdjointArgs &t, const int32_t *pbody, const int32_t *pmap,
+                           int32_t pbase, int32_t np, cudaStream_t s) {
+  if (a.nbodies <= 0) return 0;
+  k_iterate_adjoint_body<<<blocks_for(a.nbodies, 4), 128, 0, s>>>(a, t);
+  k_contact_adjoint<<<blocks_for(np, 256), 256, 0, s>>>(a, t, pbody, pmap, pbase, np);
+  return 2;
+}
+
+int launch_predict_adjoint(const TangentPredictArgs &a, cudaStream_t s) {
+  if (a.np <= 0) return 0;
+  k_predict_adjoint<<<blocks_for(a.np, 256), 256, 0, s>>>(a);
   return 1;
 }
 

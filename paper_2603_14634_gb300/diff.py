@@ -1,17 +1,22 @@
-"""Differentiable PBD-R on the GPU through forward-mode tangents.
+"""Differentiable PBD-R on the GPU: forward-mode tangents and reverse-mode
+adjoints of the substep.
 
 ``pbdr_step_tangent`` advances a scene and a tangent (dX, dV) of its state
 together: the derivative of the substep map (Algorithm 1) along one
 direction of the initial state.  Many directions of one scene run as copies
 of that scene in ONE batched call, so a whole Jacobian over a few rigid
-parameters per body costs one batched run.
+parameters per body costs one batched run.  ``pbdr_adjoint`` takes the
+gradient of a scalar loss of the final state back to the initial state
+(checkpoints every ``checkpoint_every`` substeps, recomputation in between),
+at a cost independent of the number of parameters.
 
 Parameters differentiated here: the initial rigid velocity of every body,
 v_b (3) and omega_b (3); its velocity field is v_b + omega_b x (x - c_b)
 (c_b = initial centre of mass).  Output: the final centre of mass of every
 body after ``steps`` substeps.  ``FinalCoM`` is a ``torch.autograd.Function``
-whose backward returns J^T g with J computed by the tangents; forward-mode
-needs no checkpoints (the tangents travel with the state).
+whose backward returns J^T g, from the tangents (``mode="forward"``: the
+Jacobian is formed in the forward pass) or from one adjoint run per backward
+call (``mode="reverse"``).
 """
 from __future__ import annotations
 
@@ -105,29 +110,85 @@ def final_com_and_jacobian(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, ste
     return com_jacobian(ctx, sc, steps, rigid_seeds(sc), stream)
 
 
+def com_loss_adjoint(scene, weights: np.ndarray) -> np.ndarray:
+    """dL/dX of L = sum_b weights_b . c_b (c_b = body centre of mass): each
+    particle of body b gets weights_b m_p / M_b.  [N, 3]."""
+    m = 1.0 / np.asarray(scene.inv_mass, np.float64)
+    out = np.zeros((scene.num_particles, 3))
+    for b, s in enumerate(body_slices(scene)):
+        out[s] = np.asarray(weights[b], np.float64)[None, :] * (m[s] / m[s].sum())[:, None]
+    return out
+
+
+def rigid_gradient(scene, vbar0: np.ndarray) -> np.ndarray:
+    """dL/d(v_b, omega_b) [B, 6] from dL/dV of the initial particle
+    velocities (V = v_b + omega_b x (x - c_b))."""
+    p = np.asarray(scene.pos, np.float64)
+    c = body_coms(scene, scene.pos)
+    vb = np.asarray(vbar0, np.float64)
+    out = np.zeros((scene.num_bodies, 6))
+    for b, s in enumerate(body_slices(scene)):
+        out[b, :3] = vb[s].sum(0)
+        out[b, 3:] = np.cross(p[s] - c[b], vb[s]).sum(0)
+    return out
+
+
+def com_gradient_reverse(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps: int,
+                         weights: np.ndarray, checkpoint_every: int = 20,
+                         stream=None) -> Tuple[np.ndarray, np.ndarray]:
+    """Final centres of mass [B, 3] and dL/d(v_b, omega_b) [B, 6] of
+    L = sum_b weights_b . c_b(final), by one adjoint run.  (L is linear in the
+    final state, so its adjoint is known before the run; for other losses,
+    step forward first, form dL/dX_final, restore the initial state with
+    write_state and then call adjoint.)"""
+    sc = _with_velocity(scene, rigid_velocity(scene, v_lin, w_ang))
+    sid = ctx.create_scene(sc)
+    ctx.write_adjoint(sid, com_loss_adjoint(sc, weights).astype(np.float32), None, stream)
+    ctx.adjoint(sid, steps, checkpoint_every, stream)
+    pos, _, err = ctx.read_state(sid, stream)
+    if err:
+        raise RuntimeError(f"device error bits {err}")
+    _, vbar0 = ctx.read_adjoint(sid, stream)
+    ctx.destroy_scene(sid)
+    return body_coms(sc, pos), rigid_gradient(sc, vbar0)
+
+
 try:   # the autograd wrapper needs torch; the rest of the module does not
     import torch
 
     class FinalCoM(torch.autograd.Function):
         """final CoMs [B, 3] = f(v_lin [B, 3], w_ang [B, 3]) through
-        ``steps`` PBD-R substeps on the GPU; backward = J^T grad with J from
-        the forward-mode tangents."""
+        ``steps`` PBD-R substeps on the GPU; backward = J^T grad, with J from
+        the forward-mode tangents (mode "forward") or by one adjoint run
+        (mode "reverse")."""
 
         @staticmethod
-        def forward(fctx, v_lin, w_ang, ctx, scene, steps):
+        def forward(fctx, v_lin, w_ang, ctx, scene, steps, mode="forward"):
             v = v_lin.detach().cpu().double().numpy()
             w = w_ang.detach().cpu().double().numpy()
-            final, J = final_com_and_jacobian(ctx, scene, v, w, int(steps))
-            fctx.save_for_backward(torch.from_numpy(J))
             fctx.B = scene.num_bodies
+            fctx.mode = mode
+            if mode == "forward":
+                final, J = final_com_and_jacobian(ctx, scene, v, w, int(steps))
+                fctx.save_for_backward(torch.from_numpy(J))
+            elif mode == "reverse":
+                final, _ = com_gradient_reverse(ctx, scene, v, w, int(steps), np.zeros((fctx.B, 3)))
+                fctx.args = (ctx, scene, v, w, int(steps))
+            else:
+                raise ValueError("mode is 'forward' or 'reverse'")
             return torch.from_numpy(final).to(v_lin.dtype)
 
         @staticmethod
         def backward(fctx, grad):
-            (J,) = fctx.saved_tensors
-            g = grad.detach().reshape(-1).double().cpu()
-            gp = (J.T @ g).reshape(fctx.B, 6)
-            return gp[:, :3].to(grad.dtype), gp[:, 3:].to(grad.dtype), None, None, None
+            g = grad.detach().double().cpu()
+            if fctx.mode == "forward":
+                (J,) = fctx.saved_tensors
+                gp = (J.T @ g.reshape(-1)).reshape(fctx.B, 6)
+            else:
+                ctx, scene, v, w, steps = fctx.args
+                _, gp = com_gradient_reverse(ctx, scene, v, w, steps, g.numpy())
+                gp = torch.from_numpy(gp)
+            return gp[:, :3].to(grad.dtype), gp[:, 3:].to(grad.dtype), None, None, None, None
 
 except ImportError:   # pragma: no cover
     FinalCoM = None

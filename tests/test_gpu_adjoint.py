@@ -1,0 +1,102 @@
+"""Reverse-mode adjoint of the substep on the GPU (pbdr_adjoint): the
+dot-product identity against the forward-mode tangents on random
+per-particle directions (contacts between bodies included), the oracle's
+central differences, free-flight closed forms, checkpoint invariance and the
+primal it leaves behind."""
+import numpy as np
+import pytest
+
+from fd_oracle import rigid_fd_jacobian, sliding_grid
+from paper_2603_14634_gb300 import diff, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _contact_scene(seed):
+    """Bodies pushed into each other: pair contacts with friction active."""
+    sc = scenes.random_bodies_scene(seed=seed, num_bodies=8)
+    sc.pos = (sc.pos * np.float32(0.75)).astype(np.float32)
+    return sc
+
+
+@pytest.mark.parametrize("which", ["sliding", "contacts"])
+def test_dot_product_identity_with_tangents(pbdr_lib, which):
+    """<xbar_T, dX_T> + <vbar_T, dV_T> = <xbar_0, dX_0> + <vbar_0, dV_0> for
+    random directions (dX_0, dV_0) and random final adjoints: the adjoint
+    kernels are the transpose of the tangent kernels."""
+    sc = sliding_grid(seed=2)[0] if which == "sliding" else _contact_scene(5)
+    rng = np.random.default_rng(0)
+    n, steps = sc.num_particles, 12
+    dx0 = rng.standard_normal((n, 3)).astype(np.float32) * 1e-2
+    dv0 = rng.standard_normal((n, 3)).astype(np.float32)
+    xbT = rng.standard_normal((n, 3)).astype(np.float32)
+    vbT = rng.standard_normal((n, 3)).astype(np.float32)
+    with pbdr_lib.Context(0) as c:
+        a = c.create_scene(sc)
+        c.write_tangent(a, dx0, dv0)
+        c.step_tangent(a, steps)
+        dxT, dvT = c.read_tangent(a)
+        pa, va, err_a = c.read_state(a)
+        b = c.create_scene(sc)
+        c.write_adjoint(b, xbT, vbT)
+        c.adjoint(b, steps, 5)
+        xb0, vb0 = c.read_adjoint(b)
+        pb, vb, err_b = c.read_state(b)
+    assert err_a == err_b == 0
+    lhs = float((xbT.astype(np.float64) * dxT).sum() + (vbT.astype(np.float64) * dvT).sum())
+    rhs = float((xb0.astype(np.float64) * dx0).sum() + (vb0.astype(np.float64) * dv0).sum())
+    assert abs(lhs - rhs) <= 2e-4 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)   # same primal trajectory
+
+
+def test_rigid_gradient_matches_oracle(pbdr_lib, orc):
+    sc, v, w = sliding_grid(seed=1)
+    steps = 48
+    wts = np.random.default_rng(1).standard_normal((sc.num_bodies, 3))
+    with pbdr_lib.Context(0) as c:
+        final, g = diff.com_gradient_reverse(c, sc, v, w, steps, wts, checkpoint_every=16)
+    J_ref = rigid_fd_jacobian(orc, sc, v, w, steps)
+    g_ref = (J_ref.T @ wts.reshape(-1)).reshape(sc.num_bodies, 6)
+    assert np.abs(g - g_ref).max() <= 5e-3 * np.abs(g_ref).max()
+
+
+def test_free_flight_gradient_closed_form(pbdr_lib):
+    p = scenes.lattice_cube(4, 0.1)
+    sc = scenes._assemble([p, p + np.array([1.0, 0.0, 0.0])], [np.zeros_like(p)] * 2, 1.0,
+                          friction=0.3, dt=1 / 240, iterations=10, radius=0.05)
+    sc.plane = (0.0, 0.0, 1.0, -100.0)
+    v = np.array([[0.3, 0.1, 0.2], [-0.4, 0.0, 0.5]])
+    w = np.array([[1.0, 0.0, 2.0], [0.0, -1.0, 0.5]])
+    wts = np.array([[1.0, -2.0, 0.5], [0.3, 0.7, -1.1]])
+    n = 40
+    with pbdr_lib.Context(0) as c:
+        _, g = diff.com_gradient_reverse(c, sc, v, w, n, wts, checkpoint_every=7)
+    assert np.allclose(g[:, :3], n / 240 * wts, rtol=1e-5, atol=1e-6)
+    assert np.abs(g[:, 3:]).max() < 1e-5
+
+
+def test_checkpoint_interval_does_not_change_the_result(pbdr_lib):
+    sc, v, w = sliding_grid(seed=7)
+    wts = np.ones((sc.num_bodies, 3))
+    res = []
+    with pbdr_lib.Context(0) as c:
+        for every in (1, 6, 25, 100):
+            res.append(diff.com_gradient_reverse(c, sc, v, w, 25, wts, checkpoint_every=every))
+    for f, g in res[1:]:
+        assert np.array_equal(f, res[0][0]) and np.array_equal(g, res[0][1])
+
+
+def test_autograd_reverse_mode(pbdr_lib, orc):
+    torch = pytest.importorskip("torch")
+    sc, v, w = sliding_grid(seed=6)
+    steps = 36
+    vt = torch.tensor(v, dtype=torch.float64, requires_grad=True)
+    wt = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    weights = torch.tensor(np.random.default_rng(0).standard_normal((sc.num_bodies, 3)))
+    with pbdr_lib.Context(0) as c:
+        out = diff.FinalCoM.apply(vt, wt, c, sc, steps, "reverse")
+        (out * weights).sum().backward()
+    J_ref = rigid_fd_jacobian(orc, sc, v, w, steps)
+    g_ref = (J_ref.T @ weights.numpy().reshape(-1)).reshape(sc.num_bodies, 6)
+    got = np.concatenate([vt.grad.numpy(), wt.grad.numpy()], 1)
+    assert np.abs(got - g_ref).max() <= 5e-3 * np.abs(g_ref).max()
