@@ -205,18 +205,21 @@ def kernel_source_sha(kernel):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per unit (particle-iteration or particle-substep) of a
-    kernel from the committed ncu summary, if it was taken on the current
-    kernel sources."""
+def ncu_figure(kernel, key="dram_bytes_per_unit"):
+    """A per-unit figure (DRAM bytes, warp instructions) of a kernel from the
+    committed ncu summary, if it was taken on the current kernel sources."""
     sha = kernel_source_sha(kernel)
     for path in glob.glob(os.path.join(ROOT, "profiles", f"*{kernel}*.md")):
         txt = open(path).read()
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-        m_val = re.search(r"dram_bytes_per_unit:\s*([0-9.]+)", txt)
+        m_val = re.search(key + r":\s*([0-9.]+)", txt)
         if m_sha and m_val and m_sha.group(1) == sha:
             return float(m_val.group(1))
     return None
+
+
+def ncu_traffic(kernel):
+    return ncu_figure(kernel, "dram_bytes_per_unit")
 
 
 # ---------------------------------------------------------------------------
@@ -414,6 +417,19 @@ def run_pbdr(args, rank, world, local_rank):
         "stage_ms_per_step": {k: round(v[0] / prof_steps, 4) for k, v in prof.items()},
         "stage_timing": f"CUDA events per stage over {prof_steps} substeps after the timed region",
     }
+    # the bound this latency-bound kernel actually meets: instruction issue
+    # (152 SMs x 4 schedulers x 1 warp instruction per cycle at the sampled
+    # SM clock), against the warp instructions per unit ncu counted
+    wi = ncu_figure(kernel, "warp_instructions_per_unit")
+    issue = None
+    if wi is not None and dom == "scene_resident":
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        peak_issue = n_sm * 4 * sm_mhz * 1e6
+        ach_issue = wi * units / sec_per_step
+        issue = {"bound": "issue", "achieved": round(ach_issue / 1e9, 1), "peak": round(peak_issue / 1e9, 1),
+                 "unit": "G warp-instructions/s", "frac": round(ach_issue / peak_issue, 4),
+                 "warp_instructions_per_unit": wi, "source": "ncu smsp__inst_executed.sum of the committed capture"}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -438,6 +454,8 @@ def run_pbdr(args, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
     }
+    if issue is not None:
+        line["roofline_issue"] = issue
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args, local_rank)
     if world == 1 and args.grad_steps > 0:
