@@ -100,3 +100,50 @@ def test_autograd_reverse_mode(pbdr_lib, orc):
     g_ref = (J_ref.T @ weights.numpy().reshape(-1)).reshape(sc.num_bodies, 6)
     got = np.concatenate([vt.grad.numpy(), wt.grad.numpy()], 1)
     assert np.abs(got - g_ref).max() <= 5e-3 * np.abs(g_ref).max()
+
+
+@pytest.mark.parametrize("flags", [scenes.CONTACT_AVG, scenes.NO_LINMOM, scenes.NO_ANGMOM,
+                                   scenes.NO_LINMOM | scenes.NO_ANGMOM])
+def test_dot_product_identity_with_flags(pbdr_lib, flags):
+    """The transpose relation holds for the averaged-contact reading and the
+    momentum ablations too."""
+    sc = _contact_scene(9)
+    sc.flags = flags
+    rng = np.random.default_rng(3)
+    n, steps = sc.num_particles, 8
+    dx0 = rng.standard_normal((n, 3)).astype(np.float32) * 1e-2
+    dv0 = rng.standard_normal((n, 3)).astype(np.float32)
+    xbT = rng.standard_normal((n, 3)).astype(np.float32)
+    vbT = rng.standard_normal((n, 3)).astype(np.float32)
+    with pbdr_lib.Context(0) as c:
+        a = c.create_scene(sc)
+        c.write_tangent(a, dx0, dv0)
+        c.step_tangent(a, steps)
+        dxT, dvT = c.read_tangent(a)
+        b = c.create_scene(sc)
+        c.write_adjoint(b, xbT, vbT)
+        c.adjoint(b, steps, 3)
+        xb0, vb0 = c.read_adjoint(b)
+    lhs = float((xbT.astype(np.float64) * dxT).sum() + (vbT.astype(np.float64) * dvT).sum())
+    rhs = float((xb0.astype(np.float64) * dx0).sum() + (vb0.astype(np.float64) * dv0).sum())
+    assert abs(lhs - rhs) <= 2e-4 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def test_batched_adjoint_equals_separate_runs(pbdr_lib):
+    """Scenes in one pbdr_adjoint call get the adjoints they get alone."""
+    scs = [sliding_grid(seed=s)[0] for s in (11, 12, 13)]
+    rng = np.random.default_rng(5)
+    bars = [rng.standard_normal((s.num_particles, 3)).astype(np.float32) for s in scs]
+    with pbdr_lib.Context(0) as c:
+        ids = [c.create_scene(s) for s in scs]
+        for sid, xb in zip(ids, bars):
+            c.write_adjoint(sid, xb, None)
+        c.adjoint(ids, 15, 4)
+        together = [c.read_adjoint(sid) for sid in ids]
+    for sc, xb, (x0, v0) in zip(scs, bars, together):
+        with pbdr_lib.Context(0) as c:
+            sid = c.create_scene(sc)
+            c.write_adjoint(sid, xb, None)
+            c.adjoint(sid, 15, 4)
+            ax, av = c.read_adjoint(sid)
+        assert np.array_equal(ax, x0) and np.array_equal(av, v0)
