@@ -678,6 +678,8 @@ int launch_class(pbdr_ctx *c, Plan &P, int k, cudaStream_t st) {
   a.ccap = L.ccap;
   a.v_off = L.v_off;
   a.part_off = L.part_off;
+  a.bcap = L.bcap;
+  a.bt_off = L.bt_off;
   a.smem_bytes = L.bytes;
   return launch_scene_substep(a, F.threads, st);
 }

@@ -194,6 +194,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
   // partial sums of the chunks: in shared memory when the scene has at most
   // ccap chunks, else in global memory
   float *part_sm = reinterpret_cast<float *>(smem + a.part_off);
+  // per-body rotation and anchor table (bcap bodies)
+  float4 *btab = reinterpret_cast<float4 *>(smem + a.bt_off);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
 
@@ -471,8 +473,17 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     //     momentum corrections -> X_{i+1}, V_{i+1}.
     // Every contact reads X_i before the barrier that ends (A), so the
     // owners may then overwrite positions (Jacobi order of Alg. 1).
-    // biter per body: [0] rotation (warm start), [6] anchor of the FP32 sums.
+    // Per body: the rotation (warm start) and the anchor of the FP32 sums, in
+    // a shared-memory table when the scene has at most bcap bodies, else in
+    // biter [0] and [6].
     const Chunk *ch = a.chunks + sp.c0;
+    const bool bt_local = B <= a.bcap;
+    auto rotp = [&](int32_t bl) -> float4 * {
+      return bt_local ? btab + 2 * bl : a.biter + (size_t)kBodyScratch * (b0 + bl);
+    };
+    auto ancp = [&](int32_t bl) -> float4 * {
+      return bt_local ? btab + 2 * bl + 1 : a.biter + (size_t)kBodyScratch * (b0 + bl) + 6;
+    };
     const int NC = sp.nc;
     const int32_t *order = a.border + b0;
     // partial-sum slots: local chunk numbering in shared memory, or the
@@ -480,9 +491,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     const bool part_local = NC <= a.ccap;
     const int32_t slot_base = a.bodies[b0].slot0;   // slots of a scene are contiguous
     for (int bl = tid; bl < B; bl += nt) {
-      float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
-      bt[0] = a.quat[b0 + bl];
-      bt[6] = a.bcom[b0 + bl];
+      *rotp(bl) = a.quat[b0 + bl];
+      *ancp(bl) = a.bcom[b0 + bl];
     }
     __syncthreads();
     const float r = sp.radius, dc = 2.f * r, mu = sp.friction;
@@ -491,7 +501,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       for (int c = warp; c < NC; c += nwarps) {
         const Chunk C = ch[c];
         const BodyRec br = a.bodies[C.body];
-        const float3 anc = f3(a.biter[(size_t)kBodyScratch * C.body + 6]);
+        const float3 anc = f3(*ancp(C.body - b0));
         const int32_t l0 = C.first - p0, l1 = l0 + C.count;
         float4 q4[kChunk / 32];
 #pragma unroll
@@ -567,8 +577,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
       for (int o = warp; o < B; o += nwarps) {
         const int32_t b = order[o];
         const BodyRec br = a.bodies[b];
-        float4 *bt = a.biter + (size_t)kBodyScratch * b;
-        const float3 anc = f3(bt[6]);
+        float4 *rp = rotp(b - b0), *ap = ancp(b - b0);
+        const float3 anc = f3(*ap);
         // first sums: the chunks' partials in chunk order (lane j adds value j)
         float red1[18];
         {
@@ -595,7 +605,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) Am[3 * rr + cc] = red1[3 + 3 * rr + cc] - ca[rr] * qs[cc];
         }
-        const float4 qrot = shape_rotation(Am, bt[0]);
+        const float4 qrot = shape_rotation(Am, *rp);
         float R[9];
         quat_mat(qrot, R);
         // goals g = R q + c -> X_asm, V_asm; second sums
@@ -668,18 +678,17 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         }
         __syncwarp();
         if (lane == 0) {
-          bt[0] = qrot;
+          *rp = qrot;
           const float3 cn = add(add(anc, cA2), mul(dt, dv));   // CoM after the correction
-          bt[6] = make_float4(cn.x, cn.y, cn.z, 0.f);
+          *ap = make_float4(cn.x, cn.y, cn.z, 0.f);
         }
         if (__any_sync(kFull, bad) && lane == 0) atomicOr(&a.scene_err[sid], (uint32_t)PBDR_EBIT_NONFINITE);
       }
       __syncthreads();
     }
     for (int bl = tid; bl < B; bl += nt) {
-      const float4 *bt = a.biter + (size_t)kBodyScratch * (b0 + bl);
-      a.quat[b0 + bl] = bt[0];
-      a.bcom[b0 + bl] = bt[6];
+      a.quat[b0 + bl] = *rotp(bl);
+      a.bcom[b0 + bl] = *ancp(bl);
     }
     // ---- write the substep's positions back ------------------------------
     for (int32_t i = tid; i < N; i += nt) {
@@ -707,6 +716,10 @@ FusedLayout fused_layout(int ncap, bool dx_shared, bool v_shared, bool part_shar
   L.ccap = part_shared ? ncap / 16 : 0;
   L.part_off = off;
   off += (size_t)L.ccap * kPartialFloats * sizeof(float);
+  off = (off + 15) & ~(size_t)15;
+  L.bcap = kFusedBodyCap;
+  L.bt_off = off;
+  off += (size_t)L.bcap * 2 * sizeof(float4);
   L.bytes = off;
   return L;
 }

@@ -20,7 +20,8 @@ constexpr uint32_t kSmFromXi = PBDR_SM_FROM_XI;
 constexpr uint32_t kSceneHasWrench = 1u << 16;
 
 constexpr uint32_t kEmptyCell = 0xFFFFFFFFu;
-constexpr int kFusedNbrCap = 32;   // neighbour slots per particle in the fused kernel
+constexpr int kFusedNbrCap = 32;
+constexpr int kFusedBodyCap = 64;   // bodies per scene whose rotation / anchor sit in shared memory   // neighbour slots per particle in the fused kernel
 constexpr int kMaxBodyParticles = 1 << 20;
 
 // Per-scene constants, read by every kernel (one 80-byte record per scene).
@@ -159,13 +160,15 @@ struct FusedArgs {
   int32_t tcap;            // largest bucket table of the interface grid
   int32_t ccap;            // chunks whose partial sums fit in shared memory
   size_t v_off, part_off;  // shared-memory offsets of V and of the partial sums
+  int32_t bcap;            // bodies whose rotation and anchor live in shared memory
+  size_t bt_off;           // shared-memory offset of that table
   size_t smem_bytes;
 };
 
 // shared-memory layout of a size class of the scene-resident kernel
 struct FusedLayout {
-  int32_t tcap, ccap;
-  size_t v_off, part_off, bytes;
+  int32_t tcap, ccap, bcap;
+  size_t v_off, part_off, bt_off, bytes;
 };
 
 // Tangent (forward-mode derivative) of the streaming form: dX, dV per
