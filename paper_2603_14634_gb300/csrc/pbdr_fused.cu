@@ -498,7 +498,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
     const float r = sp.radius, dc = 2.f * r, mu = sp.friction;
     const float3 nrm = make_float3(sp.nx, sp.ny, sp.nz);
     for (int it = 0; it < sp.iterations; ++it) {
-      for (int c = warp; c < NC; c += nwarps) {
+      // chunks (largest first) dealt to warps in snake order: round r goes
+      // forward when r is even, backward when odd, which evens out the load
+      for (int rd = 0, c = warp; c < NC; ++rd, c = rd * nwarps + ((rd & 1) ? nwarps - 1 - warp : warp)) {
         const Chunk C = ch[c];
         const BodyRec br = a.bodies[C.body];
         const float3 anc = f3(*ancp(C.body - b0));
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         }
       }
       __syncthreads();   // every contact of this iteration has read X_i
-      for (int o = warp; o < B; o += nwarps) {
+      for (int rd = 0, o = warp; o < B; ++rd, o = rd * nwarps + ((rd & 1) ? nwarps - 1 - warp : warp)) {
         const int32_t b = order[o];
         const BodyRec br = a.bodies[b];
         float4 *rp = rotp(b - b0), *ap = ancp(b - b0);
