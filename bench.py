@@ -456,6 +456,18 @@ def run_pbdr(args, rank, world, local_rank):
     }
     if issue is not None:
         line["roofline_issue"] = issue
+    # the same throughput priced by the streaming form's byte model (state
+    # streamed every iteration: 100 + 4 kbar B per particle-iteration plus
+    # (184 + 4 kbar) / K per substep), which the fused kernel keeps on chip;
+    # the compulsory-byte figure above is the kernel's own roofline
+    K = work_per_step / max(n_particles, 1)
+    b_model = 100.0 + 4.0 * kbar + (184.0 + 4.0 * kbar) / K
+    line["streaming_model_equivalent"] = {
+        "bytes_per_particle_iteration": round(b_model, 2),
+        "equivalent_GBps": round(b_model * value / world / 1e9, 1), "peak": peak,
+        "frac": round(b_model * value / world / 1e9 / peak, 4),
+        "what": "per-GPU throughput x bytes a state-streaming substep would move (not DRAM traffic)",
+    }
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args, local_rank)
     if world == 1 and args.grad_steps > 0:
