@@ -218,6 +218,10 @@ int pbdr_set_option(pbdr_ctx *ctx, int32_t option, int64_t value);
 int pbdr_step_tangent(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int32_t substeps,
                       void *stream);
 
+/* Sets the tangent of one scene's friction coefficient mu (default 0): the
+ * friction terms then carry d(mu pen) = dmu pen + mu d(pen).  Synchronous. */
+int pbdr_write_tangent_friction(pbdr_ctx *ctx, pbdr_scene scene, float dmu, void *stream);
+
 /* Sets the tangent of one scene: dpos, dvel host [N*3] in the caller's
  * particle order (NULL = zero).  Stream-ordered on `stream`; the host
  * buffers must stay valid until the stream reaches this point. */
@@ -256,6 +260,12 @@ int pbdr_write_adjoint(pbdr_ctx *ctx, pbdr_scene scene, const float *xbar, const
 /* Reads one scene's adjoint into host [N*3] arrays (NULL = skip) and
  * synchronises `stream`.  PBDR_ERR_INVALID before any adjoint exists. */
 int pbdr_read_adjoint(pbdr_ctx *ctx, pbdr_scene scene, float *xbar, float *vbar, void *stream);
+
+/* dLoss/dmu of one scene after pbdr_adjoint: the friction terms of every
+ * particle's corrections over all substeps and iterations, accumulated per
+ * particle on the device (no atomics) and summed here in FP64.  Zero after
+ * pbdr_write_adjoint.  Synchronises `stream`. */
+int pbdr_read_adjoint_friction(pbdr_ctx *ctx, pbdr_scene scene, double *mubar, void *stream);
 
 /* Launch shapes of the scene-resident kernel for the scene set ids[0..n):
  * out[5k..5k+4] = {particle capacity, scenes, threads per CTA, scratch bits

@@ -33,6 +33,7 @@ EXPORTS = [
     "pbdr_neighbors_noalloc", "pbdr_set_option", "pbdr_plan_config",
     "pbdr_step_tangent", "pbdr_write_tangent", "pbdr_read_tangent",
     "pbdr_adjoint", "pbdr_write_adjoint", "pbdr_read_adjoint",
+    "pbdr_write_tangent_friction", "pbdr_read_adjoint_friction",
 ]
 NUM_STAGES = 6
 STAGES = ("wrench", "predict_keys", "radix_sort", "cells_neighbors", "iterate", "scene_resident")
@@ -95,6 +96,8 @@ def load(path: Optional[str] = None):
     L.pbdr_adjoint.argtypes = [vp, P(i32), i32, i32, i32, vp]
     L.pbdr_write_adjoint.argtypes = [vp, i32, vp, vp, vp]
     L.pbdr_read_adjoint.argtypes = [vp, i32, vp, vp, vp]
+    L.pbdr_write_tangent_friction.argtypes = [vp, i32, C.c_float, vp]
+    L.pbdr_read_adjoint_friction.argtypes = [vp, i32, P(C.c_double), vp]
     L.pbdr_scene_info.argtypes = [vp, i32, P(i32), P(i32)]
     L.pbdr_last_error.argtypes = []
     L.pbdr_last_error.restype = C.c_char_p
@@ -239,6 +242,16 @@ def pbdr_read_adjoint(ctx: int, scene: int, stream=None):
     vb = np.empty((n, 3), np.float32)
     _check(load().pbdr_read_adjoint(ctx, scene, _ptr(xb), _ptr(vb), _stream(stream)))
     return xb, vb
+
+
+def pbdr_write_tangent_friction(ctx: int, scene: int, dmu: float, stream=None) -> None:
+    _check(load().pbdr_write_tangent_friction(ctx, scene, float(dmu), _stream(stream)))
+
+
+def pbdr_read_adjoint_friction(ctx: int, scene: int, stream=None) -> float:
+    out = C.c_double()
+    _check(load().pbdr_read_adjoint_friction(ctx, scene, C.byref(out), _stream(stream)))
+    return out.value
 
 
 def pbdr_scene_info(ctx: int, scene: int):
@@ -418,6 +431,12 @@ class Context:
 
     def read_adjoint(self, sid: int, stream=None):
         return pbdr_read_adjoint(self.h, sid, stream)
+
+    def write_tangent_friction(self, sid: int, dmu: float, stream=None):
+        pbdr_write_tangent_friction(self.h, sid, dmu, stream)
+
+    def read_adjoint_friction(self, sid: int, stream=None) -> float:
+        return pbdr_read_adjoint_friction(self.h, sid, stream)
 
     def build_neighbors(self, ids, stream=None):
         if isinstance(ids, (int, np.integer)):

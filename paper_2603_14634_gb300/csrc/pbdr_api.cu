@@ -177,6 +177,7 @@ struct pbdr_ctx {
   DevBuf X[2], V[2], Q, Xinit, pbody, nbr_cnt, nbr;
   DevBuf Xd[2], Vd[2];             // tangents of X, V (forward-mode derivative), lazily allocated
   DevBuf Xb[2], Vb[2], Ub;         // adjoints of X, V and of the contact corrections (reverse mode)
+  DevBuf dmu;                      // per scene: tangent of the friction coefficient
   DevBuf adj_store;                // saved states of the reverse sweep
   DevBuf bodies, wrench, quat, bcom, biter, border;
   DevBuf dx_scratch, tickets, chunks, partials;
@@ -756,6 +757,7 @@ int tangent_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
     ia.Vout = out ? V1 : V0;
     ia.k = k;
     TangentArgs ta{};
+    ta.dmu = c->dmu.p ? c->dmu.as<float>() : nullptr;
     ta.Xdin = out ? D0 : D1;
     ta.Vdin = out ? W0 : W1;
     ta.Xdout = out ? D1 : D0;
@@ -1466,6 +1468,8 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   }
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
+  if (c->dmu.p && (size_t)(sid + 1) * 4 <= c->dmu.bytes)
+    CUDA_TRY(cudaMemset(c->dmu.as<float>() + sid, 0, 4));
   if (c->Xb[0].p && N > 0) {   // adjoints in use: the new scene starts with zero adjoints
     if ((rc = ensure_adjoint(c))) return rc;
     for (DevBuf *b : {&c->Xb[0], &c->Xb[1], &c->Vb[0], &c->Vb[1], &c->Ub})
@@ -1627,6 +1631,11 @@ int pbdr_step_tangent(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t sub
   Plan *P = nullptr;
   if ((rc = build_plan(c, ids, n, &P, 1))) return rc;
   if ((rc = ensure_tangent(c))) return rc;
+  if (c->dmu.p && c->dmu.bytes < (size_t)c->scap * 4) {
+    const size_t old = c->dmu.bytes;
+    if ((rc = dev_grow(c, c->dmu, (size_t)c->scap * 4, old))) return rc;
+    CUDA_TRY(cudaMemset(c->dmu.as<unsigned char>() + old, 0, c->dmu.bytes - old));
+  }
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = activate(c, P, s))) return rc;
   int64_t launches = 0;
@@ -1659,6 +1668,41 @@ int pbdr_read_tangent(pbdr_ctx *c, pbdr_scene s, float *dpos, float *dvel, void 
   if (c->sh[s].np == 0) return PBDR_OK;
   return transfer_states(c, &s, 1, dpos, dvel, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream,
                          c->Xd[0].as<float4>(), c->Vd[0].as<float4>());
+}
+
+int pbdr_write_tangent_friction(pbdr_ctx *c, pbdr_scene s, float dmu, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (!std::isfinite(dmu)) return fail(PBDR_ERR_INVALID, "friction tangent must be finite");
+  const size_t need = (size_t)std::max(c->scap, 1) * 4;
+  if (c->dmu.bytes < need) {
+    const size_t old = c->dmu.p ? c->dmu.bytes : 0;
+    if ((rc = dev_grow(c, c->dmu, need, old))) return rc;
+    CUDA_TRY(cudaMemset(c->dmu.as<unsigned char>() + old, 0, c->dmu.bytes - old));
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->dmu.as<float>() + s, &dmu, 4, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the source is a stack value
+  return PBDR_OK;
+}
+
+int pbdr_read_adjoint_friction(pbdr_ctx *c, pbdr_scene s, double *mubar, void *stream) {
+  g_err.clear();
+  int rc = check_scene(c, s);
+  if (rc) return rc;
+  if (!mubar) return fail(PBDR_ERR_INVALID, "NULL mubar");
+  if (!c->Xb[0].p) return fail(PBDR_ERR_INVALID, "no adjoint has been written");
+  const SceneHost &S = c->sh[s];
+  std::vector<float4> h((size_t)S.np);
+  if (S.np > 0) {
+    CUDA_TRY(cudaMemcpyAsync(h.data(), c->Xb[0].as<float4>() + S.p0, (size_t)S.np * sizeof(float4),
+                             cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  double acc = 0.0;
+  for (const float4 &v : h) acc += (double)v.w;
+  *mubar = acc;
+  return PBDR_OK;
 }
 
 int pbdr_adjoint(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, int32_t checkpoint_every,

@@ -177,6 +177,7 @@ struct FusedLayout {
 struct TangentArgs {
   const float4 *Xdin, *Vdin;
   float4 *Xdout, *Vdout;
+  const float *dmu;        // per scene: tangent of the friction coefficient (nullptr: 0)
 };
 
 struct TangentPredictArgs {
@@ -194,7 +195,9 @@ struct TangentPredictArgs {
 // (IterArgs::Xin/Vin, quat and bcom as they were before it); Xout/Vout serve
 // as scratch for X_bsm, V_bsm.
 struct AdjointArgs {
-  const float4 *Xbin, *Vbin;   // adjoint of X_{i+1}, V_{i+1}
+  const float4 *Xbin, *Vbin;   // adjoint of X_{i+1}, V_{i+1}; Xb.w accumulates, per
+                               // particle, the adjoint of the friction coefficient
+                               // over the friction terms of its own correction
   float4 *Xbout, *Vbout;       // adjoint of X_i, V_i
   float4 *U;                   // per particle: adjoint of the contact correction dX (xyz),
                                // the particle's contact weight (w)

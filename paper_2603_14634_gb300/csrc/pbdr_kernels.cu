@@ -407,8 +407,10 @@ __device__ __forceinline__ float3 friction_cut_d(float3 del, float3 del_d, float
   return (mp_d / lt - f * lt_d / lt) * t + f * t_d;   // sliding: mu pen along t/|t|
 }
 
+// dmu: tangent of the friction coefficient (mu pen -> mu' pen + mu pen')
 __device__ __forceinline__ float3 contact_dx_d(const IterArgs &a, const TangentArgs &t, const ScenePar &sp,
-                                               int32_t p, float4 xp, float4 vp, float3 xpd, float3 vpd) {
+                                               int32_t p, float4 xp, float4 vp, float3 xpd, float3 vpd,
+                                               float dmu) {
   const float r = sp.radius, d_c = 2.f * r, mu = sp.friction, dt = sp.dt;
   const float3 n = make_float3(sp.nx, sp.ny, sp.nz);
   const float3 zero = make_float3(0.f, 0.f, 0.f);
@@ -416,7 +418,7 @@ __device__ __forceinline__ float3 contact_dx_d(const IterArgs &a, const TangentA
   const float pen_g = r - (dot(n, f3(xp)) - sp.nd);
   if (pen_g > 0.f) {
     const float pen_d = -dot(n, xpd);
-    dXd = pen_d * n - friction_cut_d(dt * f3(vp), dt * vpd, n, zero, mu * pen_g, mu * pen_d);
+    dXd = pen_d * n - friction_cut_d(dt * f3(vp), dt * vpd, n, zero, mu * pen_g, mu * pen_d + dmu * pen_g);
   }
   const int32_t cnt = a.nbr_cnt[p];
   float3 acc = zero;
@@ -437,7 +439,8 @@ __device__ __forceinline__ float3 contact_dx_d(const IterArgs &a, const TangentA
       const float s = xp.w / (xp.w + xq.w);
       const float3 del = dt * (f3(vp) - f3(vq));
       const float3 del_d = dt * (vpd - f3(t.Vdin[q]));
-      acc = acc + s * ((-d_d) * nh + pen * nh_d - friction_cut_d(del, del_d, nh, nh_d, mu * pen, -mu * d_d));
+      acc = acc + s * ((-d_d) * nh + pen * nh_d -
+                       friction_cut_d(del, del_d, nh, nh_d, mu * pen, -mu * d_d + dmu * pen));
       ++active;
     }
   }
@@ -476,6 +479,7 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     return;
   }
   const float dt = sp.dt, idt = sp.inv_dt;
+  const float dmu = t.dmu ? t.dmu[br.scene] : 0.f;
   const float3 anc = f3(a.bcom[b]);   // a constant reference point: no tangent
 
   // (1) contacts -> X_bsm, V_bsm and tangents; first sums and their tangents
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     const float4 xp = a.Xin[p], vp = a.Vin[p];
     const float3 xpd = f3(t.Xdin[p]), vpd = f3(t.Vdin[p]);
     const float3 dX = contact_dx(a, sp, p, xp, vp);
-    const float3 dXd = contact_dx_d(a, t, sp, p, xp, vp, xpd, vpd);
+    const float3 dXd = contact_dx_d(a, t, sp, p, xp, vp, xpd, vpd, dmu);
     const float3 xb = f3(xp) + dX;
     const float3 vb = f3(vp) + idt * dX;
     const float3 xbd = xpd + dXd;
@@ -932,7 +936,7 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
       vbb = vbb + m * cross(Lbb, e);
     }
     (void)cb;
-    t.Xbout[p] = make_float4(xbb.x, xbb.y, xbb.z, 0.f);
+    t.Xbout[p] = make_float4(xbb.x, xbb.y, xbb.z, t.Xbin[p].w);   // w: friction adjoint, carried
     t.Vbout[p] = make_float4(vbb.x, vbb.y, vbb.z, 0.f);
     const float3 u = xbb + idt * vbb;
     t.U[p] = make_float4(u.x, u.y, u.z, contact_weight(a, sp, p, a.Xin[p]));
@@ -976,7 +980,9 @@ __global__ void __launch_bounds__(256) k_contact_adjoint(IterArgs a, AdjointArgs
   const float4 xp = a.Xin[p], vp = a.Vin[p];
   const float4 up4 = t.U[p];
   const float3 up = f3(up4);
-  float3 xb = f3(t.Xbout[p]), vb = f3(t.Vbout[p]);
+  const float4 xbout = t.Xbout[p];
+  float3 xb = f3(xbout), vb = f3(t.Vbout[p]);
+  float mub = xbout.w;   // friction adjoint of this particle's own terms
   // ground term: J^T u column by column
   const float pen_g = r - (dot(n, f3(xp)) - sp.nd);
   if (pen_g > 0.f) {
@@ -993,6 +999,8 @@ __global__ void __launch_bounds__(256) k_contact_adjoint(IterArgs a, AdjointArgs
     }
     xb = xb + make_float3(gx[0], gx[1], gx[2]);
     vb = vb + make_float3(gv[0], gv[1], gv[2]);
+    // d(ground term)/d(mu) = -d f / d(mu pen) * pen
+    mub += dot(up, zero - friction_cut_d(del, zero, n, zero, mu * pen_g, pen_g));
   }
   // pair terms over the symmetric list
   const int32_t cnt = a.nbr_cnt[p];
@@ -1009,8 +1017,16 @@ __global__ void __launch_bounds__(256) k_contact_adjoint(IterArgs a, AdjointArgs
     pair_vjp(diff, f3(vp) - f3(a.Vin[q]), d_c, mu, dt, ab, gd, gw);
     xb = xb + gd;
     vb = vb + gw;
+    {   // this particle's pair term s_p T: d T / d(mu) = -d f / d(mu pen) * pen
+      const float d = sqrtf(dd);
+      const float pen = d_c - d;
+      const float3 nh = (1.f / d) * diff;
+      const float3 del = dt * (f3(vp) - f3(a.Vin[q]));
+      const float3 zero3 = make_float3(0.f, 0.f, 0.f);
+      mub += (xp.w / sw * up4.w) * dot(up, zero3 - friction_cut_d(del, zero3, nh, zero3, mu * pen, pen));
+    }
   }
-  t.Xbout[p] = make_float4(xb.x, xb.y, xb.z, 0.f);
+  t.Xbout[p] = make_float4(xb.x, xb.y, xb.z, mub);
   t.Vbout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
 }
 
@@ -1020,9 +1036,10 @@ __global__ void __launch_bounds__(256) k_predict_adjoint(TangentPredictArgs a) {
   if (i >= a.np) return;
   const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
   const ScenePar sp = a.scenes[a.bodies[a.pbody[p]].scene];
-  const float3 xb = f3(a.Xd0[p]);
+  const float4 xb4 = a.Xd0[p];
+  const float3 xb = f3(xb4);
   const float3 vb = f3(a.Vd0[p]) + sp.dt * xb;
-  a.Xdp[p] = make_float4(xb.x, xb.y, xb.z, 0.f);
+  a.Xdp[p] = make_float4(xb.x, xb.y, xb.z, xb4.w);   // w: friction adjoint, carried
   a.Vdp[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
 }
 

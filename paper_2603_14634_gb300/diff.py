@@ -63,12 +63,15 @@ def rigid_seeds(scene) -> List[np.ndarray]:
     return seeds
 
 
-def com_jacobian(ctx, scene, steps: int, seeds: List[np.ndarray], stream=None,
+MU = "mu"   # seed: the friction coefficient
+
+
+def com_jacobian(ctx, scene, steps: int, seeds: List, stream=None,
                  batch: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:
     """Final body centres of mass [B, 3] and their Jacobian [3B, S] along
-    the velocity seeds dV (each [N, 3]).  Every seed runs as one copy of the
-    scene; copies go through ``pbdr_step_tangent`` together (``batch`` at a
-    time)."""
+    the seeds: velocity tangents dV ([N, 3] each) or ``MU`` (the friction
+    coefficient).  Every seed runs as one copy of the scene; copies go
+    through ``pbdr_step_tangent`` together (``batch`` at a time)."""
     batch = batch or len(seeds)
     m = 1.0 / np.asarray(scene.inv_mass, np.float64)
     sl = body_slices(scene)
@@ -78,7 +81,11 @@ def com_jacobian(ctx, scene, steps: int, seeds: List[np.ndarray], stream=None,
         group = seeds[at:at + batch]
         ids = [ctx.create_scene(scene) for _ in group]
         for sid, dv in zip(ids, group):
-            ctx.write_tangent(sid, None, np.asarray(dv, np.float32), stream)
+            if isinstance(dv, str):
+                ctx.write_tangent(sid, None, None, stream)
+                ctx.write_tangent_friction(sid, 1.0, stream)
+            else:
+                ctx.write_tangent(sid, None, np.asarray(dv, np.float32), stream)
         ctx.step_tangent(ids, steps, stream)
         for j, sid in enumerate(ids):
             dpos, _ = ctx.read_tangent(sid, stream)
@@ -102,12 +109,14 @@ def _with_velocity(scene, vel: np.ndarray):
 
 
 def final_com_and_jacobian(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps: int,
-                           stream=None) -> Tuple[np.ndarray, np.ndarray]:
+                           stream=None, with_mu: bool = False) -> Tuple[np.ndarray, np.ndarray]:
     """Final centres of mass [B, 3] of the scene started with per-body rigid
     velocities (v_lin, w_ang) [B, 3] each, and d(final CoM)/d(v, omega)
-    [3B, 6B] (parameter order of ``rigid_seeds``)."""
+    [3B, 6B] (parameter order of ``rigid_seeds``), with a last column
+    d/d(mu) when ``with_mu``."""
     sc = _with_velocity(scene, rigid_velocity(scene, v_lin, w_ang))
-    return com_jacobian(ctx, sc, steps, rigid_seeds(sc), stream)
+    seeds = rigid_seeds(sc) + ([MU] if with_mu else [])
+    return com_jacobian(ctx, sc, steps, seeds, stream)
 
 
 def com_loss_adjoint(scene, weights: np.ndarray) -> np.ndarray:
@@ -135,12 +144,13 @@ def rigid_gradient(scene, vbar0: np.ndarray) -> np.ndarray:
 
 def com_gradient_reverse(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps: int,
                          weights: np.ndarray, checkpoint_every: int = 20,
-                         stream=None) -> Tuple[np.ndarray, np.ndarray]:
+                         stream=None, with_mu: bool = False):
     """Final centres of mass [B, 3] and dL/d(v_b, omega_b) [B, 6] of
-    L = sum_b weights_b . c_b(final), by one adjoint run.  (L is linear in the
-    final state, so its adjoint is known before the run; for other losses,
-    step forward first, form dL/dX_final, restore the initial state with
-    write_state and then call adjoint.)"""
+    L = sum_b weights_b . c_b(final), by one adjoint run (and dL/dmu as a
+    third value when ``with_mu``).  L is linear in the final state, so its
+    adjoint is known before the run; for other losses, step forward first,
+    form dL/dX_final, restore the initial state with write_state and then
+    call adjoint."""
     sc = _with_velocity(scene, rigid_velocity(scene, v_lin, w_ang))
     sid = ctx.create_scene(sc)
     ctx.write_adjoint(sid, com_loss_adjoint(sc, weights).astype(np.float32), None, stream)
@@ -149,7 +159,10 @@ def com_gradient_reverse(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps
     if err:
         raise RuntimeError(f"device error bits {err}")
     _, vbar0 = ctx.read_adjoint(sid, stream)
+    mubar = ctx.read_adjoint_friction(sid, stream) if with_mu else None
     ctx.destroy_scene(sid)
+    if with_mu:
+        return body_coms(sc, pos), rigid_gradient(sc, vbar0), mubar
     return body_coms(sc, pos), rigid_gradient(sc, vbar0)
 
 

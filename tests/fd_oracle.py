@@ -42,3 +42,13 @@ def sliding_grid(seed=0, nx=2, n=4, mu=0.3, speed=(1.0, 1.5), spin=1.0):
     w[:, 2] = (rng.random(B) * 2 - 1) * spin
     sc.vel = diff.rigid_velocity(sc, v, w).astype(np.float32)
     return sc, v, w
+
+
+def mu_fd(orc, scene, steps, h=1e-4):
+    """d(final CoM [3B]) / d(mu) by central differences (FP64)."""
+    out = []
+    for sgn in (1.0, -1.0):
+        sc = scenes.Scene(**{**scene.__dict__})
+        sc.friction = float(scene.friction) + sgn * h
+        out.append(final_coms(orc, sc, steps).reshape(-1))
+    return (out[0] - out[1]) / (2 * h)

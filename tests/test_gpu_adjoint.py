@@ -6,7 +6,7 @@ primal it leaves behind."""
 import numpy as np
 import pytest
 
-from fd_oracle import rigid_fd_jacobian, sliding_grid
+from fd_oracle import mu_fd, rigid_fd_jacobian, sliding_grid
 from paper_2603_14634_gb300 import diff, scenes
 
 pytestmark = pytest.mark.gpu
@@ -147,3 +147,23 @@ def test_batched_adjoint_equals_separate_runs(pbdr_lib):
             c.adjoint(sid, 15, 4)
             ax, av = c.read_adjoint(sid)
         assert np.array_equal(ax, x0) and np.array_equal(av, v0)
+
+
+def test_friction_derivative_forward_reverse_and_oracle(pbdr_lib, orc):
+    """d(final CoMs)/d(mu): forward tangent (seed dmu = 1) against the
+    oracle's central differences; dL/dmu of the adjoint against the tangent
+    column (L = weights . CoMs)."""
+    sc, v, w = sliding_grid(seed=1)
+    steps = 48
+    wts = np.random.default_rng(2).standard_normal((sc.num_bodies, 3))
+    with pbdr_lib.Context(0) as c:
+        _, J = diff.final_com_and_jacobian(c, sc, v, w, steps, with_mu=True)
+        _, g, mubar = diff.com_gradient_reverse(c, sc, v, w, steps, wts, checkpoint_every=16,
+                                                with_mu=True)
+    dmu = J[:, -1]
+    ref = mu_fd(orc, scenes.Scene(**{**sc.__dict__}), steps)
+    assert np.abs(dmu - ref).max() <= 5e-3 * np.abs(ref).max()
+    want = float(wts.reshape(-1) @ dmu)
+    assert abs(mubar - want) <= 1e-4 * max(abs(want), 1e-6), (mubar, want)
+    assert np.abs(g - (J[:, :-1].T @ wts.reshape(-1)).reshape(sc.num_bodies, 6)).max() <= \
+        1e-4 * np.abs(g).max()

@@ -4,7 +4,7 @@ box sliding with kinetic friction (Table I, Test 1 kinematics)."""
 import numpy as np
 import pytest
 
-from fd_oracle import final_coms, rigid_fd_jacobian, sliding_grid
+from fd_oracle import final_coms, mu_fd, rigid_fd_jacobian, sliding_grid
 from paper_2603_14634_gb300 import diff, scenes
 
 
@@ -31,15 +31,16 @@ def test_free_flight_derivative_is_n_dt(orc):
 
 
 def test_sliding_box_derivative_closed_form(orc):
-    """A box sliding at |v| along x with kinetic friction moves
-    x(T) = v T - mu g T^2 / 2 along its velocity: d x / d v_x = T, and a
-    sideways perturbation turns the path, d y / d v_y = T - mu g T^2 / (2|v|)."""
-    steps, mu, speed = 48, 0.3, 1.5
-    T = steps / 240
+    """A box sliding at speed s along x with kinetic friction loses mu g dt
+    of speed per substep, so after n substeps it has moved
+    x_n = n s dt - mu g dt^2 n (n + 1) / 2 along its velocity (the discrete
+    form of x = s T - mu g T^2 / 2): d x / d v_x = n dt, and a sideways
+    perturbation turns the path, d y / d v_y = n dt - mu g dt^2 n (n + 1) / (2 s)."""
+    n, mu, speed, dt = 48, 0.3, 1.5, 1 / 240
     sc = _box((speed, 0.0, 0.0), mu=mu)
-    J = rigid_fd_jacobian(orc, sc, np.array([[speed, 0.0, 0.0]]), np.zeros((1, 3)), steps)
-    assert J[0, 0] == pytest.approx(T, rel=5e-3)
-    assert J[1, 1] == pytest.approx(T - mu * scenes.GRAVITY * T * T / (2 * speed), rel=2e-2)
+    J = rigid_fd_jacobian(orc, sc, np.array([[speed, 0.0, 0.0]]), np.zeros((1, 3)), n)
+    assert J[0, 0] == pytest.approx(n * dt, rel=5e-4)
+    assert J[1, 1] == pytest.approx(n * dt - mu * scenes.GRAVITY * dt * dt * n * (n + 1) / (2 * speed), rel=5e-4)
     assert abs(J[1, 0]) < 1e-8 and abs(J[0, 1]) < 1e-8
 
 
@@ -51,3 +52,13 @@ def test_fd_step_size_is_converged(orc):
     J1 = rigid_fd_jacobian(orc, sc, v, w, steps, h=1e-4)
     J2 = rigid_fd_jacobian(orc, sc, v, w, steps, h=1e-5)
     assert np.abs(J1 - J2).max() < 1e-5 * max(1.0, np.abs(J1).max())
+
+
+def test_sliding_box_friction_derivative_closed_form(orc):
+    """With x_n = n s dt - mu g dt^2 n (n + 1) / 2 (see above),
+    d x / d mu = -g dt^2 n (n + 1) / 2."""
+    n, mu, speed, dt = 48, 0.3, 1.5, 1 / 240
+    sc = _box((speed, 0.0, 0.0), mu=mu)
+    d = mu_fd(orc, sc, n)
+    assert d[0] == pytest.approx(-0.5 * scenes.GRAVITY * dt * dt * n * (n + 1), rel=5e-4)
+    assert abs(d[1]) < 1e-8
