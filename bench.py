@@ -505,14 +505,14 @@ def run_gradient(args, local_rank):
         diff.com_gradient_reverse(c, sc, v, w, 3, wts)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, J = diff.final_com_and_jacobian(c, sc, v, w, args.grad_steps)
+        _, J = diff.final_com_and_jacobian(c, sc, v, w, args.grad_steps, with_mu=True)
         secs = time.perf_counter() - t0
         t0 = time.perf_counter()
-        diff.com_gradient_reverse(c, sc, v, w, args.grad_steps, wts, checkpoint_every=20)
+        diff.com_gradient_reverse(c, sc, v, w, args.grad_steps, wts, checkpoint_every=20, with_mu=True)
         secs_rev = time.perf_counter() - t0
     dirs = J.shape[1]
     return {
-        "what": "d(final body CoMs)/d(initial v_b, omega_b), 16 bodies of 5^3: full Jacobian by forward-mode tangents (all directions batched), and one gradient by the reverse-mode adjoint (checkpoints every 20 substeps)",
+        "what": "d(final body CoMs)/d(initial v_b, omega_b, friction mu), 16 bodies of 5^3: full Jacobian by forward-mode tangents (all directions batched), and one gradient by the reverse-mode adjoint (checkpoints every 20 substeps)",
         "outputs": int(J.shape[0]), "directions": int(dirs), "substeps": args.grad_steps,
         "jacobian_ms": round(secs * 1e3, 2),
         "tangent_particle_iters_per_s": round(dirs * sc.num_particles * sc.iterations * args.grad_steps / secs, 1),
