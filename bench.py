@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
+    ap.add_argument("--path", choices=["resident", "streaming"], default="resident",
+                    help="timed path: scene-resident kernel where scenes fit (default) or the "
+                         "streaming form for every scene")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch shapes instead of tuned ones")
     ap.add_argument("--grad-steps", type=int, default=200,
@@ -80,6 +83,7 @@ def workload_config(scs, args, extra=None):
                      f"particles, seed {args.seed}, r=0.05 m, mu=0.5, dt=1/240 s, 10 iterations"),
         "scenes": len(scs), "particles": n, "bodies": b, "iterations": 10, "dt": 1.0 / 240.0,
         "step": "one PBD-R substep of all scenes in one batched pbdr_step",
+        "path": getattr(args, "path", "resident"),
         "state": (f"after {args.settle} settling substeps ({args.settle / 240.0:.2f} s simulated) "
                   "from the seeded start, so bodies rest on the ground and on each other"),
         "l2": "inputs larger than L2 (state ~%d MB >> 129 MB)" % (n * 80 // (1 << 20)),
@@ -92,7 +96,10 @@ def workload_config(scs, args, extra=None):
 
 def make_workload(args, seed):
     from paper_2603_14634_gb300 import scenes
-    return scenes.batched_scenes(args.scenes, seed=seed, workers=min(os.cpu_count() or 1, 32))
+    # ranks of one node share the host cores
+    local = max(1, int(os.environ.get("LOCAL_WORLD_SIZE", "1")))
+    return scenes.batched_scenes(args.scenes, seed=seed,
+                                 workers=max(1, min((os.cpu_count() or 1) // local, 32)))
 
 
 # ---------------------------------------------------------------------------
@@ -242,6 +249,8 @@ def run_pbdr(args, rank, world, local_rank):
     if args.no_autotune:
         from paper_2603_14634_gb300.binding import OPT_AUTOTUNE
         ctx.set_option(OPT_AUTOTUNE, 0)
+    if args.path == "streaming":
+        ctx.set_path(streaming=True)
     ids = [ctx.create_scene(s) for s in scs]
     plan_cfg = None
     n_particles = sum(s.num_particles for s in scs)
@@ -346,7 +355,7 @@ def run_pbdr(args, rank, world, local_rank):
         b0.record(stream)
         torch.cuda.synchronize()
         streaming_value = work_per_step * n_stream_steps / (a0.elapsed_time(b0) * 1e-3)
-    ctx.set_path(streaming=False)
+    ctx.set_path(streaming=args.path == "streaming")
 
     # ---- one scene per launch on a sample of the same scenes ----
     sample = ids[:: max(1, len(ids) // max(1, args.per_scene_sample))][: args.per_scene_sample]
