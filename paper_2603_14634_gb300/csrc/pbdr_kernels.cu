@@ -191,8 +191,8 @@ __device__ __forceinline__ float3 friction_cut(float3 del, float3 n, float mu_pe
   return f * dt_;
 }
 
-__device__ __forceinline__ float3 contact_dx(const IterArgs &a, const ScenePar &sp, int32_t p,
-                                             float4 xp, float4 vp) {
+__device__ __forceinline__ float3 contact_dx_n(const IterArgs &a, const ScenePar &sp, int32_t p,
+                                               float4 xp, float4 vp, int32_t cnt) {
   const float r = sp.radius, d_c = 2.f * r, mu = sp.friction, dt = sp.dt;
   const float3 n = make_float3(sp.nx, sp.ny, sp.nz);
   float3 dX = make_float3(0.f, 0.f, 0.f);
@@ -203,7 +203,6 @@ __device__ __forceinline__ float3 contact_dx(const IterArgs &a, const ScenePar &
     dX = pen_g * n - friction_cut(del, n, mu * pen_g);
   }
   // particle-particle over the ascending candidate list
-  const int32_t cnt = a.nbr_cnt[p];
   float3 acc = make_float3(0.f, 0.f, 0.f);
   int active = 0;
   for (int32_t j = 0; j < cnt; ++j) {
@@ -226,9 +225,16 @@ __device__ __forceinline__ float3 contact_dx(const IterArgs &a, const ScenePar &
   return dX + acc;
 }
 
+__device__ __forceinline__ float3 contact_dx(const IterArgs &a, const ScenePar &sp, int32_t p,
+                                             float4 xp, float4 vp) {
+  return contact_dx_n(a, sp, p, xp, vp, a.nbr_cnt[p]);
+}
+
 // ---------------------------------------------------------------------------
 // one solver iteration, one body per warp
 // ---------------------------------------------------------------------------
+
+constexpr int kIterBatch = 4;   // particles per lane whose loads are issued together
 
 __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
   const int lane = threadIdx.x & 31;
@@ -253,28 +259,48 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
 
   // (1) contacts from X_i (Jacobi) -> X_bsm, V_bsm ; first body reduction
   float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
-  for (int32_t p = p0 + lane; p < pe; p += 32) {
-    const float4 xp = a.Xin[p], vp = a.Vin[p];
-    const float3 dX = contact_dx(a, sp, p, xp, vp);
-    const float3 xb = f3(xp) + dX;
-    float3 vb;
-    if (std_vel)
-      vb = idt * (xb - f3(a.Xinit[p]));
-    else
-      vb = f3(vp) + idt * dX;   // V_i + dX/dt (Sec. III-B)
-    a.Xout[p] = make_float4(xb.x, xb.y, xb.z, xp.w);
-    a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
-    const float4 q = a.Q[p];
-    const float m = q.w;
-    const float3 e = xb - anc;
-    const float3 me = m * e;
-    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
-    sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
-    sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
-    sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
-    sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
-    const float3 l = cross(me, vb);
-    sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
+  // Each lane takes particles p0 + lane + 32 j in order of j; the loads of
+  // kIterBatch of them are issued together (X_in, V_in, Q and the list
+  // lengths are read-only here), so one memory round trip covers a batch.
+  for (int32_t pb = p0 + lane; pb < pe; pb += 32 * kIterBatch) {
+    float4 xr[kIterBatch], vr[kIterBatch], qr[kIterBatch];
+    int32_t cr[kIterBatch];
+#pragma unroll
+    for (int u = 0; u < kIterBatch; ++u) {
+      const int32_t p = pb + 32 * u;
+      if (p < pe) {
+        xr[u] = __ldg(a.Xin + p);
+        vr[u] = __ldg(a.Vin + p);
+        qr[u] = __ldg(a.Q + p);
+        cr[u] = __ldg(a.nbr_cnt + p);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIterBatch; ++u) {
+      const int32_t p = pb + 32 * u;
+      if (p >= pe) break;
+      const float4 xp = xr[u], vp = vr[u];
+      const float3 dX = contact_dx_n(a, sp, p, xp, vp, cr[u]);
+      const float3 xb = f3(xp) + dX;
+      float3 vb;
+      if (std_vel)
+        vb = idt * (xb - f3(a.Xinit[p]));
+      else
+        vb = f3(vp) + idt * dX;   // V_i + dX/dt (Sec. III-B)
+      a.Xout[p] = make_float4(xb.x, xb.y, xb.z, xp.w);
+      a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
+      const float4 q = qr[u];
+      const float m = q.w;
+      const float3 e = xb - anc;
+      const float3 me = m * e;
+      sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
+      sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
+      sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
+      sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
+      sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
+      const float3 l = cross(me, vb);
+      sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
+    }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -306,30 +332,45 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
   // (2) shape-matching goals g = R q + c -> X_asm, V_asm ; second reduction
   float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f};
   float sXX[6] = {0.f};
-  for (int32_t p = p0 + lane; p < pe; p += 32) {
-    const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
-    const float4 q = a.Q[p];
-    const float m = q.w;
-    const float3 grel = make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z,
-                                    R[3] * q.x + R[4] * q.y + R[5] * q.z,
-                                    R[6] * q.x + R[7] * q.y + R[8] * q.z) + cA;
-    const float3 dsm = grel - (f3(xb4) - anc);
-    const float3 xa = f3(xb4) + dsm;
-    float3 va;
-    if (std_vel)
-      va = idt * (xa - f3(a.Xinit[p]));
-    else
-      va = f3(vb4) + idt * dsm;
-    a.Xout[p] = make_float4(xa.x, xa.y, xa.z, xb4.w);
-    a.Vout[p] = make_float4(va.x, va.y, va.z, 0.f);
-    const float3 e = xa - anc;
-    const float3 me = m * e;
-    sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
-    sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
-    const float3 l = cross(me, va);
-    sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
-    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
-    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+  for (int32_t pb = p0 + lane; pb < pe; pb += 32 * kIterBatch) {
+    float4 xr[kIterBatch], vr[kIterBatch], qr[kIterBatch];
+#pragma unroll
+    for (int u = 0; u < kIterBatch; ++u) {   // this thread's own pass-(1) results
+      const int32_t p = pb + 32 * u;
+      if (p < pe) {
+        xr[u] = a.Xout[p];
+        vr[u] = a.Vout[p];
+        qr[u] = __ldg(a.Q + p);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIterBatch; ++u) {
+      const int32_t p = pb + 32 * u;
+      if (p >= pe) break;
+      const float4 xb4 = xr[u], vb4 = vr[u];
+      const float4 q = qr[u];
+      const float m = q.w;
+      const float3 grel = make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z,
+                                      R[3] * q.x + R[4] * q.y + R[5] * q.z,
+                                      R[6] * q.x + R[7] * q.y + R[8] * q.z) + cA;
+      const float3 dsm = grel - (f3(xb4) - anc);
+      const float3 xa = f3(xb4) + dsm;
+      float3 va;
+      if (std_vel)
+        va = idt * (xa - f3(a.Xinit[p]));
+      else
+        va = f3(vb4) + idt * dsm;
+      a.Xout[p] = make_float4(xa.x, xa.y, xa.z, xb4.w);
+      a.Vout[p] = make_float4(va.x, va.y, va.z, 0.f);
+      const float3 e = xa - anc;
+      const float3 me = m * e;
+      sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
+      sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
+      const float3 l = cross(me, va);
+      sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
+      sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
+      sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+    }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -359,15 +400,29 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
 
   // (3) apply the uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
   bool bad = false;
-  for (int32_t p = p0 + lane; p < pe; p += 32) {
-    const float4 xa4 = a.Xout[p], va4 = a.Vout[p];
-    const float3 r = (f3(xa4) - anc) - cA2;
-    const float3 corr = dv - cross(om, r);
-    const float3 v = f3(va4) + corr;
-    const float3 x = f3(xa4) + dt * corr;
-    a.Xout[p] = make_float4(x.x, x.y, x.z, xa4.w);
-    a.Vout[p] = make_float4(v.x, v.y, v.z, 0.f);
-    bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
+  for (int32_t pb = p0 + lane; pb < pe; pb += 32 * kIterBatch) {
+    float4 xr[kIterBatch], vr[kIterBatch];
+#pragma unroll
+    for (int u = 0; u < kIterBatch; ++u) {
+      const int32_t p = pb + 32 * u;
+      if (p < pe) {
+        xr[u] = a.Xout[p];
+        vr[u] = a.Vout[p];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIterBatch; ++u) {
+      const int32_t p = pb + 32 * u;
+      if (p >= pe) break;
+      const float4 xa4 = xr[u], va4 = vr[u];
+      const float3 r = (f3(xa4) - anc) - cA2;
+      const float3 corr = dv - cross(om, r);
+      const float3 v = f3(va4) + corr;
+      const float3 x = f3(xa4) + dt * corr;
+      a.Xout[p] = make_float4(x.x, x.y, x.z, xa4.w);
+      a.Vout[p] = make_float4(v.x, v.y, v.z, 0.f);
+      bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
+    }
   }
   if (lane == 0) {
     a.quat[b] = qrot;
