@@ -199,7 +199,7 @@ struct pbdr_ctx {
   // autotuned launch shapes by (size class, scenes in it): threads, dx, v, grid
   std::map<std::pair<int, int32_t>, std::array<int, 4>> tune_memo;
   // tables of the active plan and the streaming form's scratch (grow-only)
-  DevBuf tab, s_keys_a, s_keys_b, s_vals_a, s_vals_b, s_hist, s_cstart, s_cend, s_spos, s_pmap, s_bmap;
+  DevBuf tab, s_keys_a, s_keys_b, s_vals_a, s_vals_b, s_hist, s_cells, s_spos, s_pmap, s_bmap;
   const Plan *active = nullptr;
   uint64_t gen = 1;                // bumped whenever a device buffer moves (graphs recapture)
   Plan *last_nbr_plan = nullptr;
@@ -525,8 +525,7 @@ int activate(pbdr_ctx *c, Plan *P, cudaStream_t s) {
         (rc = dev_alloc(c, c->s_vals_a, npb * 4)) || (rc = dev_alloc(c, c->s_vals_b, npb * 4)) ||
         (rc = dev_alloc(c, c->s_spos, npb * sizeof(float4))) ||
         (rc = dev_alloc(c, c->s_hist, radix_hist_words(S->np) * 4)) ||
-        (rc = dev_alloc(c, c->s_cstart, (size_t)std::max<uint32_t>(S->T_total, 1) * 4)) ||
-        (rc = dev_alloc(c, c->s_cend, (size_t)std::max<uint32_t>(S->T_total, 1) * 4)))
+        (rc = dev_alloc(c, c->s_cells, (size_t)std::max<uint32_t>(S->T_total, 1) * sizeof(uint4))))
       return rc;
     if (!S->pcontig && (rc = dev_alloc(c, c->s_pmap, npb * 4))) return rc;
     if (!S->bcontig && (rc = dev_alloc(c, c->s_bmap, (size_t)std::max(S->nb, 1) * 4))) return rc;
@@ -584,7 +583,8 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   }
   P.sorted_in_b = in_b;
   StageTimer tm(c, s, 3, launches);
-  CUDA_TRY(cudaMemsetAsync(c->s_cstart.p, 0xFF, (size_t)std::max<uint32_t>(P.T_total, 1) * 4, s));
+  // every bucket record to all ones: empty, and the identities of its body minima
+  CUDA_TRY(cudaMemsetAsync(c->s_cells.p, 0xFF, (size_t)std::max<uint32_t>(P.T_total, 1) * sizeof(uint4), s));
   const uint32_t *sk = in_b ? c->s_keys_b.as<uint32_t>() : c->s_keys_a.as<uint32_t>();
   const uint32_t *sv = in_b ? c->s_vals_b.as<uint32_t>() : c->s_vals_a.as<uint32_t>();
   CellArgs ca{};
@@ -592,8 +592,7 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   ca.svals = sv;
   ca.Xp = Xp;
   ca.pbody = c->pbody.as<int32_t>();
-  ca.cstart = c->s_cstart.as<uint32_t>();
-  ca.cend = c->s_cend.as<uint32_t>();
+  ca.cells = c->s_cells.as<uint4>();
   ca.spos = c->s_spos.as<float4>();
   ca.np = P.np;
   launches += launch_cells(ca, s);
@@ -605,8 +604,7 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   na.pmap = P.pcontig ? nullptr : c->s_pmap.as<int32_t>();
   na.pbase = P.pbase;
   na.spos = c->s_spos.as<float4>();
-  na.cstart = c->s_cstart.as<uint32_t>();
-  na.cend = c->s_cend.as<uint32_t>();
+  na.cells = c->s_cells.as<uint4>();
   na.bodies = c->bodies.as<BodyRec>();
   na.scenes = c->scenes.as<ScenePar>();
   na.hbase = reinterpret_cast<const uint32_t *>(c->tab.as<int32_t>() + P.o_hbase);

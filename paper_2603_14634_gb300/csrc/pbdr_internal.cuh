@@ -92,7 +92,7 @@ struct CellArgs {
   const uint32_t *skeys, *svals;
   const float4 *Xp;
   const int32_t *pbody;
-  uint32_t *cstart, *cend;
+  uint4 *cells;            // per bucket: first, end, lowest body, ~highest body
   float4 *spos;            // sorted (x, y, z, body id bits)
   int32_t np;
 };
@@ -104,7 +104,7 @@ struct NbrArgs {
   const int32_t *pbody;
   const int32_t *pmap;     // plan particle -> global particle (nullptr: pbase + i)
   int32_t pbase;
-  const uint32_t *cstart, *cend;
+  const uint4 *cells;
   const BodyRec *bodies;
   const ScenePar *scenes;
   const uint32_t *hbase;

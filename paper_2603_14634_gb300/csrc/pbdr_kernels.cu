@@ -9,7 +9,8 @@
 // Kernels of one substep (Algorithm 1):
 //   k_predict   integration and the hashed-grid cell key of x~
 //   (radix sort of (key, particle))
-//   k_cells     bucket [start, end) ranges and positions in sorted order
+//   k_cells     bucket records ([start, end), body bounds) and positions in
+//               sorted order
 //   k_neighbors candidate lists N(p) with the exact FP32 predicate (ELL)
 //   k_iterate   one solver iteration for one body per warp:
 //               contacts -> X_bsm, V_bsm; shape matching -> X_asm, V_asm;
@@ -96,15 +97,24 @@ __global__ void __launch_bounds__(256) k_predict(PredictArgs a) {
 // bucket ranges of the sorted keys + positions gathered in sorted order
 // ---------------------------------------------------------------------------
 
+// A bucket record holds [first, end) of the bucket in sorted order and the
+// lowest and (bitwise NOT of the) highest body id among its particles; the
+// records start as all ones (empty bucket, identities of both minima), so
+// the body bounds come from integer minima and do not depend on the order
+// of the updates.
 __global__ void __launch_bounds__(256) k_cells(CellArgs a) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.np) return;
   const uint32_t key = a.skeys[i];
-  if (i == 0 || a.skeys[i - 1] != key) a.cstart[key] = (uint32_t)i;
-  if (i == a.np - 1 || a.skeys[i + 1] != key) a.cend[key] = (uint32_t)(i + 1);
+  uint32_t *rec = reinterpret_cast<uint32_t *>(a.cells + key);
+  if (i == 0 || a.skeys[i - 1] != key) rec[0] = (uint32_t)i;
+  if (i == a.np - 1 || a.skeys[i + 1] != key) rec[1] = (uint32_t)(i + 1);
   const uint32_t p = a.svals[i];
+  const int32_t body = a.pbody[p];
+  atomicMin(rec + 2, (uint32_t)body);
+  atomicMin(rec + 3, ~(uint32_t)body);
   const float4 x = a.Xp[p];
-  a.spos[i] = make_float4(x.x, x.y, x.z, __int_as_float(a.pbody[p]));
+  a.spos[i] = make_float4(x.x, x.y, x.z, __int_as_float(body));
 }
 
 // ---------------------------------------------------------------------------
@@ -132,15 +142,17 @@ __global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
   int cnt = 0;
   // each of the 27 cells once; a bucket shared by several cells (hash
   // collision) is scanned once per cell and only that cell's particles are
-  // taken, so no candidate appears twice
+  // taken, so no candidate appears twice.  A bucket that holds particles of
+  // the particle's own body only (most buckets around a body's interior) has
+  // no candidate and is not scanned.
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
         const int32_t cx = ix + dx, cy = iy + dy, cz = iz + dz;
-        const uint32_t bkt = hb + (cell_hash(cx, cy, cz) & mask);
-        const uint32_t st = a.cstart[bkt];
-        if (st == kEmptyCell) continue;
-        const uint32_t en = a.cend[bkt];
+        const uint4 rec = __ldg(a.cells + hb + (cell_hash(cx, cy, cz) & mask));
+        if (rec.x == kEmptyCell) continue;
+        if (rec.z == (uint32_t)bp && ~rec.w == (uint32_t)bp) continue;
+        const uint32_t st = rec.x, en = rec.y;
         for (uint32_t j = st; j < en; ++j) {
           const float4 xq = a.spos[j];
           if (__float_as_int(xq.w) == bp) continue;
