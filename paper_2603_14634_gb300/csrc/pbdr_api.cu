@@ -975,16 +975,16 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
     return PBDR_OK;
   };
   // every candidate starts from the same saved state: one warm substep,
-  // then the fastest of two timed pairs of substeps
+  // then the fastest of three timed runs of three substeps
   auto time_substeps = [&](float *ms) -> int {
     int64_t l = 0;
     int r2 = restore();
     if (r2) return r2;
     if ((r2 = fused_substep(c, P, s, l))) return r2;
     *ms = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       CUDA_TRY(cudaEventRecord(e0, s));
-      for (int k = 0; k < 2; ++k)
+      for (int k = 0; k < 3; ++k)
         if ((r2 = fused_substep(c, P, s, l))) return r2;
       CUDA_TRY(cudaEventRecord(e1, s));
       CUDA_TRY(cudaEventSynchronize(e1));
@@ -1050,7 +1050,7 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
     // time: single trials differ by about as much as close candidates do
     std::sort(cands.begin(), cands.end(), [](const Cand &x, const Cand &y) { return x.ms < y.ms; });
     const size_t top = std::min<size_t>(3, cands.size());
-    for (int round = 0; round < 2; ++round)
+    for (int round = 0; round < 3; ++round)
       for (size_t i = 0; i < top; ++i) {
         float ms = 0.f;
         apply(cands[i]);
