@@ -168,6 +168,13 @@ int set_last_error(int code, const char *msg) {
 
 struct pbdr_ctx {
   int device = 0;
+  // Library work per stream: an event recorded after the last call that
+  // enqueued work on that stream.  pbdr_destroy_scene queries them to tell
+  // whether the ranges it frees may still be in use on the device.
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> work_ev;
+  bool work_pending = false;   // some recorded work may not have completed
+  bool work_unknown = false;   // an event could not be recorded: assume work in flight
+  bool free_dirty = false;     // freed ranges may still be used by work in flight
   size_t budget = 0;
   size_t used = 0;
   int32_t pcap = 0, bcap = 0, scap = 0;
@@ -242,6 +249,49 @@ void dev_free(pbdr_ctx *c, DevBuf &b) {
   c->used -= b.bytes;
   b.release();
 }
+
+// records that library work was enqueued on stream s
+void note_work(pbdr_ctx *c, cudaStream_t s) {
+  cudaEvent_t e = nullptr;
+  for (auto &w : c->work_ev)
+    if (w.first == s) e = w.second;
+  if (!e) {
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      c->work_unknown = c->work_pending = true;
+      return;
+    }
+    c->work_ev.push_back({s, e});
+  }
+  if (cudaEventRecord(e, s) != cudaSuccess) {
+    cudaGetLastError();
+    c->work_unknown = true;
+  }
+  c->work_pending = true;
+}
+
+// true when every library call's work has completed (queries, never waits)
+bool work_done(pbdr_ctx *c) {
+  if (!c->work_pending) return true;
+  if (c->work_unknown) return false;
+  for (auto &w : c->work_ev) {
+    const cudaError_t q = cudaEventQuery(w.second);
+    if (q == cudaSuccess) continue;
+    if (q != cudaErrorNotReady) cudaGetLastError();
+    return false;
+  }
+  c->work_pending = false;
+  return true;
+}
+
+// notes, when a call that took a stream returns, the work it enqueued there
+struct WorkNote {
+  pbdr_ctx *c;
+  cudaStream_t s;
+  ~WorkNote() {
+    if (c) note_work(c, s);
+  }
+};
 
 // grow `b` to `bytes`, keeping the first `keep` bytes
 int dev_grow(pbdr_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
@@ -1270,6 +1320,7 @@ int pbdr_ctx_destroy(pbdr_ctx *c) {
   cudaDeviceSynchronize();
   invalidate_plans(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (auto &w : c->work_ev) cudaEventDestroy(w.second);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (int k = 0; k < 4; ++k) {
     if (c->cls_stream[k]) cudaStreamDestroy(c->cls_stream[k]);
@@ -1442,8 +1493,12 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   std::vector<float4> quat(B, make_float4(0.f, 0.f, 0.f, 1.f));
   std::vector<BodyWrench> wr(B);
   std::memset(wr.data(), 0, sizeof(BodyWrench) * (size_t)B);
-  // a reused scene slot or table range may still be in use by steps in flight
-  if (!p_top || !b_top || !c_top || sid < (int32_t)c->sh.size()) CUDA_TRY(cudaDeviceSynchronize());
+  // a reused scene slot or table range may still be in use by work that was
+  // in flight when it was freed: then wait for the device
+  if ((!p_top || !b_top || !c_top || sid < (int32_t)c->sh.size()) && c->free_dirty) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    c->free_dirty = c->work_pending = c->work_unknown = false;
+  }
   if (N > 0) {
     CUDA_TRY(cudaMemcpy(c->X[0].as<float4>() + S.p0, X.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->V[0].as<float4>() + S.p0, V.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
@@ -1478,6 +1533,10 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]})
       CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
   }
+  // the copies from pageable host memory and the memsets above run on the
+  // legacy default stream, which work on non-blocking streams does not wait
+  // for: complete them before returning
+  CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
   if ((int32_t)c->bh.size() < B0 + B) {
     c->bh.resize(B0 + B);
     c->wh.resize(B0 + B);
@@ -1502,6 +1561,10 @@ int pbdr_destroy_scene(pbdr_ctx *c, pbdr_scene s) {
   g_err.clear();
   int rc = check_scene(c, s);
   if (rc) return rc;
+  // the ranges freed here are clean once every call's work has completed
+  // (e.g. after a read of the results); otherwise the next call that reuses
+  // a freed range waits for the device first
+  c->free_dirty = !work_done(c);
   SceneHost &S = c->sh[s];
   S.alive = false;
   c->pa.give(S.p0, S.np);
@@ -1534,12 +1597,14 @@ int pbdr_set_body_wrench(pbdr_ctx *c, pbdr_scene s, int32_t body, const float F[
   else
     S.par.flags &= ~kSceneHasWrench;
   CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + s, &S.par, sizeof(ScenePar), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));   // the copies complete before later work on any stream
   if (was != c->bh[gb].has_wrench) drop_plans_with(c, s);
   return PBDR_OK;
 }
 
 int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   if (substeps < 0) return fail(PBDR_ERR_INVALID, "substeps must be >= 0");
   Plan *P = nullptr;
@@ -1582,6 +1647,7 @@ int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, v
 
 int pbdr_read_state(pbdr_ctx *c, pbdr_scene s, float *pos, float *vel, uint32_t *err_bits, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (c->sh[s].np == 0) {
@@ -1596,6 +1662,7 @@ int pbdr_read_state(pbdr_ctx *c, pbdr_scene s, float *pos, float *vel, uint32_t 
 
 int pbdr_write_state(pbdr_ctx *c, pbdr_scene s, const float *pos, const float *vel, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (c->sh[s].np == 0) return PBDR_OK;
@@ -1605,17 +1672,20 @@ int pbdr_write_state(pbdr_ctx *c, pbdr_scene s, const float *pos, const float *v
 int pbdr_read_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *pos, float *vel,
                      uint32_t *err_bits, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   return transfer_states(c, ids, n, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
 }
 
 int pbdr_write_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, const float *pos, const float *vel,
                       void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   return transfer_states(c, ids, n, nullptr, nullptr, pos, vel, nullptr, 1, (cudaStream_t)stream);
 }
 
 int pbdr_step_tangent(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   if (substeps < 0) return fail(PBDR_ERR_INVALID, "substeps must be >= 0");
   int rc = check_ids(c, ids, n);
@@ -1645,6 +1715,7 @@ int pbdr_step_tangent(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t sub
 
 int pbdr_write_tangent(pbdr_ctx *c, pbdr_scene s, const float *dpos, const float *dvel, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if ((rc = ensure_tangent(c))) return rc;
@@ -1660,6 +1731,7 @@ int pbdr_write_tangent(pbdr_ctx *c, pbdr_scene s, const float *dpos, const float
 
 int pbdr_read_tangent(pbdr_ctx *c, pbdr_scene s, float *dpos, float *dvel, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (!c->Xd[0].p) return fail(PBDR_ERR_INVALID, "no tangent has been written");
@@ -1670,6 +1742,7 @@ int pbdr_read_tangent(pbdr_ctx *c, pbdr_scene s, float *dpos, float *dvel, void 
 
 int pbdr_write_tangent_friction(pbdr_ctx *c, pbdr_scene s, float dmu, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (!std::isfinite(dmu)) return fail(PBDR_ERR_INVALID, "friction tangent must be finite");
@@ -1686,6 +1759,7 @@ int pbdr_write_tangent_friction(pbdr_ctx *c, pbdr_scene s, float dmu, void *stre
 
 int pbdr_read_adjoint_friction(pbdr_ctx *c, pbdr_scene s, double *mubar, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (!mubar) return fail(PBDR_ERR_INVALID, "NULL mubar");
@@ -1706,6 +1780,7 @@ int pbdr_read_adjoint_friction(pbdr_ctx *c, pbdr_scene s, double *mubar, void *s
 int pbdr_adjoint(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, int32_t checkpoint_every,
                  void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   if (substeps < 0) return fail(PBDR_ERR_INVALID, "substeps must be >= 0");
   if (checkpoint_every < 1) return fail(PBDR_ERR_INVALID, "checkpoint_every must be >= 1");
@@ -1760,6 +1835,7 @@ int pbdr_adjoint(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps
 
 int pbdr_write_adjoint(pbdr_ctx *c, pbdr_scene s, const float *xbar, const float *vbar, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if ((rc = ensure_adjoint(c))) return rc;
@@ -1775,6 +1851,7 @@ int pbdr_write_adjoint(pbdr_ctx *c, pbdr_scene s, const float *xbar, const float
 
 int pbdr_read_adjoint(pbdr_ctx *c, pbdr_scene s, float *xbar, float *vbar, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (!c->Xb[0].p) return fail(PBDR_ERR_INVALID, "no adjoint has been written");
@@ -1794,6 +1871,7 @@ int pbdr_scene_info(pbdr_ctx *c, pbdr_scene s, int32_t *np, int32_t *nb) {
 
 int pbdr_build_neighbors(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   Plan *P = nullptr;
   int rc = build_plan(c, ids, n, &P, 1);
@@ -1814,6 +1892,7 @@ int pbdr_build_neighbors(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, void *st
 int pbdr_read_neighbors(pbdr_ctx *c, pbdr_scene s, uint32_t *sorted_key, uint32_t *sorted_id, int32_t *off,
                         int32_t *idx, int64_t idx_cap, int64_t *idx_count, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   int rc = check_scene(c, s);
   if (rc) return rc;
   if (!idx_count) return fail(PBDR_ERR_INVALID, "NULL idx_count");
@@ -1880,6 +1959,7 @@ int pbdr_read_neighbors(pbdr_ctx *c, pbdr_scene s, uint32_t *sorted_key, uint32_
 
 int pbdr_neighbor_total(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int64_t *total, void *stream) {
   g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
   if (!c || !ids || !total || n < 1) return fail(PBDR_ERR_INVALID, "NULL argument");
   CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int64_t t = 0;

@@ -114,3 +114,37 @@ def test_two_contexts_in_lockstep_stay_identical(pbdr_lib):
     finally:
         for c, _ in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("read_before_destroy", [False, True])
+def test_reuse_of_ranges_freed_with_work_in_flight_or_done(pbdr_lib, read_before_destroy):
+    """A scene is destroyed either while its substeps may still run on the
+    device (the next scene that takes its ranges must wait for them) or
+    after its results were read (no wait: the next scene is created while
+    another scene's substeps run on the side stream).  Either way the new
+    scene, which takes the destroyed one's slot and ranges, ends
+    bit-identical to the same scene stepped alone."""
+    torch = pytest.importorskip("torch")
+    a_sc = scenes.random_bodies_scene(seed=7, num_bodies=20)
+    b_sc = scenes.random_bodies_scene(seed=8, num_bodies=20)
+    other = scenes.random_bodies_scene(seed=9, num_bodies=40)
+    with pbdr_lib.Context(0) as c:
+        c.set_option(pbdr_lib.OPT_AUTOTUNE, 0)
+        st = torch.cuda.Stream()
+        o = c.create_scene(other)
+        a = c.create_scene(a_sc)
+        c.step([o, a], 30, st.cuda_stream)
+        if read_before_destroy:
+            c.read_state(a, st.cuda_stream)
+        c.destroy_scene(a)
+        c.step(o, 30, st.cuda_stream)        # keeps the device busy
+        b = c.create_scene(b_sc)
+        assert b == a                         # the freed slot (and ranges) are reused
+        c.step([o, b], 6, st.cuda_stream)
+        pos, vel, err = c.read_state(b, st.cuda_stream)
+        opos, ovel, oerr = c.read_state(o, st.cuda_stream)
+    wpos, wvel, werr = _alone(pbdr_lib, b_sc, 6, False)
+    assert err == werr == 0 and oerr == 0
+    assert np.array_equal(pos, wpos) and np.array_equal(vel, wvel)
+    upos, uvel, _ = _alone(pbdr_lib, other, 66, False)
+    assert np.array_equal(opos, upos) and np.array_equal(ovel, uvel)
