@@ -97,16 +97,23 @@ int pbdr_ctx_create(int device, size_t hbm_budget_bytes, pbdr_ctx **out);
 /* Frees every device resource of the context.  NULL is accepted. */
 int pbdr_ctx_destroy(pbdr_ctx *ctx);
 
-/* Copies a scene into device memory (synchronous) and returns its handle.
- * Computes M_b, c_b and the rest offsets in FP64 on the host.  Slots and
- * table ranges of destroyed scenes are reused; a call that reuses one first
- * waits for the device to finish the work already queued.
+/* Copies a scene into device memory (synchronous: the copies have landed
+ * when it returns) and returns its handle.  Computes M_b, c_b and the rest
+ * offsets in FP64 on the host.  Slots and table ranges of destroyed scenes
+ * are reused; a call that reuses one that was freed while library work was
+ * still in flight (see pbdr_destroy_scene) first waits for the device to
+ * finish the work already queued, otherwise it does not wait, and work of
+ * other scenes may run meanwhile on non-blocking streams.
  * Errors: PBDR_ERR_INVALID (descriptor check failed: sizes, offsets, masses,
  * radius, dt, iterations, plane normal), PBDR_ERR_BUDGET, PBDR_ERR_OOM,
  * PBDR_ERR_UNSUPPORTED (flags). */
 int pbdr_create_scene(pbdr_ctx *ctx, const pbdr_scene_desc *desc, pbdr_scene *out);
 
-/* Removes a scene from the context; its handle becomes invalid. */
+/* Removes a scene from the context; its handle becomes invalid.  Never
+ * waits: it checks (without blocking) whether the work of every earlier call
+ * that took a stream has completed, e.g. after a pbdr_read_state(s) of the
+ * results; if not, the next pbdr_create_scene that reuses the freed slot or
+ * ranges waits for the device. */
 int pbdr_destroy_scene(pbdr_ctx *ctx, pbdr_scene scene);
 
 /* Sets a constant external force F (N) at the centre of mass and a constant
