@@ -256,6 +256,20 @@ void note_work(pbdr_ctx *c, cudaStream_t s) {
   for (auto &w : c->work_ev)
     if (w.first == s) e = w.second;
   if (!e) {
+    // streams come and go (a caller may destroy its own): forget those whose
+    // last work has completed before the list grows long
+    if (c->work_ev.size() >= 16) {
+      for (size_t k = 0; k < c->work_ev.size();) {
+        if (cudaEventQuery(c->work_ev[k].second) == cudaSuccess) {
+          cudaEventDestroy(c->work_ev[k].second);
+          c->work_ev[k] = c->work_ev.back();
+          c->work_ev.pop_back();
+        } else {
+          cudaGetLastError();
+          ++k;
+        }
+      }
+    }
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       c->work_unknown = c->work_pending = true;
