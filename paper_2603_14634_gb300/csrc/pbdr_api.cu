@@ -1507,50 +1507,58 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   std::vector<float4> quat(B, make_float4(0.f, 0.f, 0.f, 1.f));
   std::vector<BodyWrench> wr(B);
   std::memset(wr.data(), 0, sizeof(BodyWrench) * (size_t)B);
-  // a reused scene slot or table range may still be in use by work that was
-  // in flight when it was freed: then wait for the device
-  if ((!p_top || !b_top || !c_top || sid < (int32_t)c->sh.size()) && c->free_dirty) {
-    CUDA_TRY(cudaDeviceSynchronize());
-    c->free_dirty = c->work_pending = c->work_unknown = false;
+  // device uploads; on failure the taken ranges go back to the free lists
+  auto upload = [&]() -> int {
+    // a reused scene slot or table range may still be in use by work that was
+    // in flight when it was freed: then wait for the device
+    if ((!p_top || !b_top || !c_top || sid < (int32_t)c->sh.size()) && c->free_dirty) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      c->free_dirty = c->work_pending = c->work_unknown = false;
+    }
+    if (N > 0) {
+      CUDA_TRY(cudaMemcpy(c->X[0].as<float4>() + S.p0, X.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->V[0].as<float4>() + S.p0, V.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->Q.as<float4>() + S.p0, Q.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->pbody.as<int32_t>() + S.p0, pb.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->bodies.as<BodyRec>() + S.b0, br.data(), (size_t)B * sizeof(BodyRec), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->quat.as<float4>() + S.b0, quat.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->bcom.as<float4>() + S.b0, com.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + S.b0, wr.data(), (size_t)B * sizeof(BodyWrench), cudaMemcpyHostToDevice));
+    }
+    if (!chk.empty())
+      CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + C0, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    if (B > 0) {   // the scene's bodies, largest first (owner-warp order of the scene-resident kernel)
+      std::vector<int32_t> ord(B);
+      for (int32_t b = 0; b < B; ++b) ord[b] = B0 + b;
+      std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+        return br[x - B0].count > br[y - B0].count;
+      });
+      CUDA_TRY(cudaMemcpy(c->border.as<int32_t>() + B0, ord.data(), (size_t)B * 4, cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
+    if (c->dmu.p && (size_t)(sid + 1) * 4 <= c->dmu.bytes)
+      CUDA_TRY(cudaMemset(c->dmu.as<float>() + sid, 0, 4));
+    if (c->Xb[0].p && N > 0) {   // adjoints in use: the new scene starts with zero adjoints
+      if ((rc = ensure_adjoint(c))) return rc;
+      for (DevBuf *b : {&c->Xb[0], &c->Xb[1], &c->Vb[0], &c->Vb[1], &c->Ub})
+        CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
+    }
+    if (c->Xd[0].p && N > 0) {   // tangents in use: the new scene starts with zero tangents
+      if ((rc = ensure_tangent(c))) return rc;
+      for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]})
+        CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
+    }
+    // the copies from pageable host memory and the memsets above run on the
+    // legacy default stream, which work on non-blocking streams does not wait
+    // for: complete them before returning
+    CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
+    return PBDR_OK;
+  };
+  if ((rc = upload())) {
+    give_back();
+    return rc;
   }
-  if (N > 0) {
-    CUDA_TRY(cudaMemcpy(c->X[0].as<float4>() + S.p0, X.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->V[0].as<float4>() + S.p0, V.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->Q.as<float4>() + S.p0, Q.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->pbody.as<int32_t>() + S.p0, pb.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->bodies.as<BodyRec>() + S.b0, br.data(), (size_t)B * sizeof(BodyRec), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->quat.as<float4>() + S.b0, quat.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->bcom.as<float4>() + S.b0, com.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + S.b0, wr.data(), (size_t)B * sizeof(BodyWrench), cudaMemcpyHostToDevice));
-  }
-  if (!chk.empty())
-    CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + C0, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
-  if (B > 0) {   // the scene's bodies, largest first (owner-warp order of the scene-resident kernel)
-    std::vector<int32_t> ord(B);
-    for (int32_t b = 0; b < B; ++b) ord[b] = B0 + b;
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
-      return br[x - B0].count > br[y - B0].count;
-    });
-    CUDA_TRY(cudaMemcpy(c->border.as<int32_t>() + B0, ord.data(), (size_t)B * 4, cudaMemcpyHostToDevice));
-  }
-  CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
-  if (c->dmu.p && (size_t)(sid + 1) * 4 <= c->dmu.bytes)
-    CUDA_TRY(cudaMemset(c->dmu.as<float>() + sid, 0, 4));
-  if (c->Xb[0].p && N > 0) {   // adjoints in use: the new scene starts with zero adjoints
-    if ((rc = ensure_adjoint(c))) return rc;
-    for (DevBuf *b : {&c->Xb[0], &c->Xb[1], &c->Vb[0], &c->Vb[1], &c->Ub})
-      CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
-  }
-  if (c->Xd[0].p && N > 0) {   // tangents in use: the new scene starts with zero tangents
-    if ((rc = ensure_tangent(c))) return rc;
-    for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]})
-      CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
-  }
-  // the copies from pageable host memory and the memsets above run on the
-  // legacy default stream, which work on non-blocking streams does not wait
-  // for: complete them before returning
-  CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
   if ((int32_t)c->bh.size() < B0 + B) {
     c->bh.resize(B0 + B);
     c->wh.resize(B0 + B);
