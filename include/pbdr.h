@@ -53,7 +53,7 @@ extern "C" {
 #define PBDR_ERR_NONFINITE (-5)    /* a non-finite position was produced */
 #define PBDR_ERR_TIMEOUT (-6)      /* a bounded device wait gave up */
 #define PBDR_ERR_CUDA (-7)         /* a CUDA runtime call failed */
-#define PBDR_ERR_UNSUPPORTED (-8)  /* a flag combination this build does not run */
+#define PBDR_ERR_UNSUPPORTED (-8)  /* a flag combination the GPU path does not implement */
 
 /* per-scene error bits reported by pbdr_read_state / pbdr_read_states */
 #define PBDR_EBIT_NBR_OVERFLOW (1u << 0) /* a neighbour list was truncated */
