@@ -413,3 +413,39 @@ def test_graph_replay_and_autotune_are_bit_identical(pbdr_lib, streaming):
     for other in outs[1:]:
         for (p0, v0), (p1, v1) in zip(outs[0], other):
             assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
+
+
+def _two_particle_scene(pos, vel, inv_mass, plane, dt):
+    pos = np.asarray(pos, np.float32)
+    return scenes.Scene(pos=pos, vel=np.asarray(vel, np.float32), inv_mass=np.asarray(inv_mass, np.float32),
+                        body_off=np.arange(pos.shape[0] + 1, dtype=np.int32), radius=0.05, friction=0.5,
+                        gravity=(0.0, 0.0, 0.0), plane=plane, dt=dt, iterations=1)
+
+
+def test_contact_and_friction_closed_form_cases(ctx, orc):
+    """The configurations whose oracle results are pinned by closed forms
+    (ground push-out, static and kinetic ground friction, pair push-out split
+    by inverse mass, static and kinetic pair friction; single-particle
+    bodies, one iteration) give the oracle's result on the GPU."""
+    far = (0.0, 0.0, 1.0, -100.0)
+    ground = (0.0, 0.0, 1.0, 0.0)
+    dt = 1.0 / 256.0
+    cases = [
+        _two_particle_scene([[0.3, -0.2, 0.06]], [[0.0, 0.0, -6.0]], [1.0], ground, 1 / 240),
+        _two_particle_scene([[0.0, 0.0, 0.06]], [[1.0, 0.0, -6.0]], [1.0], ground, 1 / 240),
+        _two_particle_scene([[0.0, 0.0, 0.06]], [[4.0, 0.0, -6.0]], [1.0], ground, 1 / 240),
+        _two_particle_scene([[-0.045, 0, 0.5], [0.045, 0, 0.5]], [[0, 0, 0], [0, 0, 0]], [1.0, 1.0], far, dt),
+        _two_particle_scene([[-0.045, 0, 0.5], [0.045, 0, 0.5]], [[0, 0, 0], [0, 0, 0]], [1.0, 1 / 3], far, dt),
+        _two_particle_scene([[-0.045, -0.25 * dt, 0.5], [0.045, 0.25 * dt, 0.5]], [[0, 0.25, 0], [0, -0.25, 0]],
+                            [1.0, 1.0], far, dt),
+        _two_particle_scene([[-0.045, -1.5 * dt, 0.5], [0.045, 1.5 * dt, 0.5]], [[0, 1.5, 0], [0, -1.5, 0]],
+                            [1.0, 1.0], far, dt),
+    ]
+    ids = [ctx.create_scene(sc) for sc in cases]
+    ctx.step(ids, 1)
+    for sid, sc in zip(ids, cases):
+        pos, vel, err = ctx.read_state(sid)
+        o = orc.OracleScene(sc).substep(1)
+        assert err == 0
+        assert np.abs(pos - o.x).max() < 1e-6, (sid, pos, o.x)
+        assert np.abs(vel - o.v).max() < 1e-3 * max(1.0, np.abs(o.v).max()), (sid, vel, o.v)
