@@ -112,3 +112,24 @@ def test_pair_beyond_contact_distance_is_untouched(orc):
     # within the neighbour radius 2.2 r but farther apart than 2r: no correction
     o = _step(orc, _scene([[-0.052, 0.0, 5.0], [0.052, 0.0, 5.0]], [[0, 1, 0], [0, -1, 0]], [1.0, 1.0], far))
     assert abs(o.x[0, 0] - _f(-0.052)) < 1e-15 and abs(o.v[0, 1] - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("avg", [False, True])
+def test_pair_sum_and_contact_averaging(orc, avg):
+    """A particle pressed by two neighbours on opposite sides takes the plain
+    sum of its two pair corrections (the summation of the contact
+    corrections in Algorithm 1), or their mean with the CONTACT_AVG flag (the
+    averaging of Macklin et al. 2014)."""
+    far = (0.0, 0.0, 1.0, -100.0)
+    xs = [0.0, 0.09, -0.095]       # overlaps 0.01 with the right and 0.005 with the left neighbour
+    sc = _scene([[x, 0.0, 5.0] for x in xs], [[0, 0, 0]] * 3, [1.0] * 3, far)
+    sc.flags = orc.CONTACT_AVG if avg else 0
+    o = _step(orc, sc)
+    pen_r = 2 * R - (_f(0.09) - _f(0.0))
+    pen_l = 2 * R - (_f(0.0) - _f(-0.095))
+    terms = [-0.5 * pen_r, 0.5 * pen_l]          # pushed left by the right one, right by the left one
+    want = sum(terms) / (2 if avg else 1)
+    assert abs(o.x[0, 0] - want) < 1e-12
+    # each outer particle has one contact: the same either way
+    assert abs(o.x[1, 0] - (_f(0.09) + 0.5 * pen_r)) < 1e-12
+    assert abs(o.x[2, 0] - (_f(-0.095) - 0.5 * pen_l)) < 1e-12
