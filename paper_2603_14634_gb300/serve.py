@@ -41,7 +41,7 @@ class Request:
     admitted: Optional[float] = None
     done: Optional[float] = None
     sid: Optional[int] = None
-    remaining: int = 0
+    due: int = 0               # batched substeps of the server after which it is done
 
 
 class Server:
@@ -78,6 +78,13 @@ class Server:
         self.host_ms = {"admit": 0.0, "step": 0.0, "retire": 0.0}
         self.ticks = 0
         self.work_done = 0            # particle-iterations
+        # bookkeeping that changes only on admission and retirement, so a
+        # tick costs O(1) host work besides the library calls
+        self._stepped = 0             # batched substeps run so far
+        self._due: Dict[int, List[Request]] = collections.defaultdict(list)
+        self._ids: List[int] = []     # scene handles of the resident requests
+        self._ids_dirty = False
+        self._tick_work = 0           # particle-iterations of one batched substep
         self._next = 0
         self.t0 = None
 
@@ -88,7 +95,7 @@ class Server:
             raise ValueError("a request needs at least one substep")
         rid = self._next
         self._next += 1
-        self.pending.append(Request(rid, scene, int(steps), float(arrival), remaining=int(steps)))
+        self.pending.append(Request(rid, scene, int(steps), float(arrival)))
         return rid
 
     def _cost(self, req: Request) -> int:
@@ -110,13 +117,17 @@ class Server:
             self.pending.popleft()
             req.sid = sid
             req.admitted = now
+            req.due = self._stepped + req.steps     # it joins the next batched substep
+            self._due[req.due].append(req)
+            self._tick_work += int(req.scene.num_particles) * int(req.scene.iterations)
+            self._ids_dirty = True
             self.ledger += cost
             self.active[req.rid] = req
             n += 1
         return n
 
     def _retire(self, now: float):
-        done = [r for r in self.active.values() if r.remaining == 0]
+        done = self._due.pop(self._stepped, [])   # in admission order
         if not done:
             return
         pos, vel, err = self.ctx.read_states([r.sid for r in done], stream=self.stream)
@@ -127,6 +138,8 @@ class Server:
             at += n
             self.ctx.destroy_scene(req.sid)
             self.ledger -= self._cost(req)
+            self._tick_work -= n * int(req.scene.iterations)
+            self._ids_dirty = True
             req.done = now
             del self.active[req.rid]
             self.finished.append(req)
@@ -137,11 +150,12 @@ class Server:
         t_0 = self.clock()
         stepped = bool(self.active)
         if stepped:
-            ids = [r.sid for r in self.active.values()]
-            self.ctx.step(ids, 1, self.stream)      # asynchronous
-            for r in self.active.values():
-                r.remaining -= 1
-                self.work_done += int(r.scene.num_particles) * int(r.scene.iterations)
+            if self._ids_dirty:
+                self._ids = [r.sid for r in self.active.values()]
+                self._ids_dirty = False
+            self.ctx.step(self._ids, 1, self.stream)   # asynchronous
+            self._stepped += 1
+            self.work_done += self._tick_work
         t_a = self.clock()
         self._admit(t_a - self.t0)                 # host work overlaps the substep
         t_b = self.clock()
