@@ -609,6 +609,12 @@ def main():
         from paper_2603_14634_gb300 import build as B
         if rank == 0 or world == 1:
             B.build()
+        else:   # rank 0 builds (the link is an atomic rename); the others wait for it
+            t0 = time.time()
+            while not B.up_to_date():
+                if time.time() - t0 > 900:
+                    raise RuntimeError("the library built by rank 0 did not appear")
+                time.sleep(0.5)
         line = run_pbdr(args, rank, world, local_rank)
     if line is not None:
         print(json.dumps(line), flush=True)

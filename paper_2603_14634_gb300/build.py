@@ -42,6 +42,11 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def up_to_date() -> bool:
+    """True when the library exists and is newer than every source."""
+    return not _stale()
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if not force and not _stale():
         return LIB
