@@ -337,11 +337,16 @@ def run_pbdr(args, rank, world, local_rank):
             ctx.read_states(ids, pos_h, vel_h, sh)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-    if dist is not None:
+    e2e_work = float(work_per_step * e2e_steps)
+    job_particles, job_scenes = n_particles, len(ids)   # summed over the ranks below
+    if dist is not None:   # slowest rank's time, all ranks' work (each rank has its own batch)
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = work_per_step * world * e2e_steps / e2e_s
+        w = torch.tensor([e2e_work, float(n_particles), float(len(ids))], device="cuda", dtype=torch.float64)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        e2e_work, job_particles, job_scenes = float(w[0]), int(w[1]), int(w[2])
+    e2e_value = e2e_work / e2e_s
 
     # ---- the streaming form (one launch per stage and per iteration) ----
     ctx.set_path(streaming=True)
@@ -453,10 +458,11 @@ def run_pbdr(args, rank, world, local_rank):
             "batched_same_sample": round(batched_sample_value, 1),
             "batched_over_per_scene": round(batched_sample_value / per_scene_value, 2)},
         "streaming_form": {"value": round(streaming_value, 1), "unit": UNIT,
-                           "what": "same batch, one launch per stage and per solver iteration"},
+                           "what": "same batch, one launch per stage and per solver iteration"
+                                   + (" (rank 0's GPU)" if world > 1 else "")},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
-                "h2d_bytes_per_step": int(n_particles * 24),
-                "d2h_bytes_per_step": int(n_particles * 24 + 4 * len(ids)), "steps": e2e_steps,
+                "h2d_bytes_per_step": int(job_particles * 24),
+                "d2h_bytes_per_step": int(job_particles * 24 + 4 * job_scenes), "steps": e2e_steps,
                 "path": "pbdr_write_states + pbdr_step + pbdr_read_states, pinned host buffers"},
         "gpu_launches": int(launches_per_step * args.steps),
         "launch_config": {"graph_per_substep": True, "autotuned_classes": plan_cfg},
