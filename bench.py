@@ -229,6 +229,31 @@ def ncu_traffic(kernel):
     return ncu_figure(kernel, "dram_bytes_per_unit")
 
 
+# FP32 operations of the method per particle, counted from the arithmetic of
+# the scene-resident kernel (an FMA counts 2): per solver iteration the
+# contact pass without contacts (ground test, X_bsm, V_bsm, 18 first sums) 61,
+# the goal pass (goals, X_asm, V_asm, 15 second sums) 81, the momentum
+# correction 27; per substep the integration 12.  Contacts, the per-body
+# rotation and momentum solves and the neighbour build are not counted.
+FLOPS_PER_PARTICLE_ITERATION = 61 + 81 + 27
+FLOPS_PER_PARTICLE_SUBSTEP = 12
+FP32_LANES_PER_SM = 128
+
+
+def alu_roofline(iterations, particles, sec_per_step, n_sm, sm_mhz):
+    """Counted FP32 throughput of one substep against the FP32 peak of the
+    SMs (lanes x 2 flop x clock)."""
+    flops_per_unit = FLOPS_PER_PARTICLE_ITERATION * iterations + FLOPS_PER_PARTICLE_SUBSTEP
+    achieved = flops_per_unit * particles / sec_per_step
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+    return {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(peak / 1e12, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "flops_per_unit": round(flops_per_unit, 1), "unit_of_work": "particle-substep",
+            "what": "counted FP32 operations of the method (iteration passes and integration; "
+                    "contacts, per-body solves and neighbour build not counted) against "
+                    "SMs x 128 FP32 lanes x 2 x max SM clock"}
+
+
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
@@ -471,6 +496,11 @@ def run_pbdr(args, rank, world, local_rank):
     }
     if issue is not None:
         line["roofline_issue"] = issue
+    if dom == "scene_resident":
+        line["roofline_alu"] = alu_roofline(
+            work_per_step / max(n_particles, 1), n_particles, sec_per_step,
+            torch.cuda.get_device_properties(local_rank).multi_processor_count,
+            (clk or {}).get("sm_max_mhz") or 2070.0)
     # the same throughput priced by the streaming form's byte model (state
     # streamed every iteration: 100 + 4 kbar B per particle-iteration plus
     # (184 + 4 kbar) / K per substep), which the fused kernel keeps on chip;
