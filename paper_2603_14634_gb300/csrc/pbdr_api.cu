@@ -156,6 +156,9 @@ constexpr int64_t kTuneAfter = 128;   // substeps of a plan before its launch sh
 
 constexpr int kClassCaps[4] = {1024, 2048, 4096, 8192};
 constexpr int kClassThreads[4] = {256, 256, 512, 512};
+// dynamic shared memory a class layout may use: the 227 KB a CTA may opt in
+// to, less 1 KB for the kernel's static shared variables
+constexpr size_t kFusedSmemLimit = 226 * 1024;
 
 }  // namespace
 
@@ -472,8 +475,8 @@ int fill_stream_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P, std
 // memory where they fit, the class's thread count, every CTA the SMs hold
 int default_shape(pbdr_ctx *c, int k, Plan::FClass &F) {
   F.ncap = kClassCaps[k];
-  F.dx_shared = fused_layout(F.ncap, true, false, true).bytes <= 220 * 1024;
-  F.v_shared = F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024;
+  F.dx_shared = fused_layout(F.ncap, true, false, true).bytes <= kFusedSmemLimit;
+  F.v_shared = F.dx_shared && fused_layout(F.ncap, true, true, true).bytes <= kFusedSmemLimit;
   F.threads = c->fused_threads ? c->fused_threads : kClassThreads[k];
   const int per_sm = fused_max_blocks_per_sm(F.ncap, F.dx_shared, F.v_shared, F.threads);
   if (per_sm < 1) return fail(PBDR_ERR_CUDA, "scene-resident kernel does not fit on an SM");
@@ -1086,10 +1089,10 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
     const int threads_c[3] = {128, 256, 512};
     for (int dxi = 0; dxi < 2; ++dxi) {
       const bool dxs = dxi == 0;
-      if (dxs && fused_layout(F.ncap, true, false, true).bytes > 220 * 1024) continue;
+      if (dxs && fused_layout(F.ncap, true, false, true).bytes > kFusedSmemLimit) continue;
       for (int vs = 0; vs < 2; ++vs) {
         const bool vsh = vs == 1;
-        if (vsh && !(dxs && fused_layout(F.ncap, true, true, true).bytes <= 220 * 1024)) continue;
+        if (vsh && !(dxs && fused_layout(F.ncap, true, true, true).bytes <= kFusedSmemLimit)) continue;
         for (int ti = 0; ti < 3; ++ti) {
           const int per_sm = fused_max_blocks_per_sm(F.ncap, dxs, vsh, threads_c[ti]);
           if (per_sm < 1) continue;

@@ -20,8 +20,8 @@ constexpr uint32_t kSmFromXi = PBDR_SM_FROM_XI;
 constexpr uint32_t kSceneHasWrench = 1u << 16;
 
 constexpr uint32_t kEmptyCell = 0xFFFFFFFFu;
-constexpr int kFusedNbrCap = 32;
-constexpr int kFusedBodyCap = 64;   // bodies per scene whose rotation / anchor sit in shared memory   // neighbour slots per particle in the fused kernel
+constexpr int kFusedNbrCap = 32;    // neighbour slots per particle in the fused kernel
+constexpr int kFusedBodyCap = 64;   // bodies per scene whose rotation / anchor sit in shared memory
 constexpr int kMaxBodyParticles = 1 << 20;
 
 // Per-scene constants, read by every kernel (one 80-byte record per scene).
@@ -59,7 +59,7 @@ struct alignas(16) Chunk {
   int32_t k;                    // index of the chunk within its body
 };
 constexpr int kBodyScratch = 12;    // float4 per body in FusedArgs::biter
-constexpr int kPartialFloats = 20;  // floats per partial-sum slot
+constexpr int kPartialFloats = 28;  // floats per partial-sum slot: 9 plain sums, 9 pairs
 
 // Per-body external wrench, set by the host (force, torque) and the
 // per-substep derived accelerations (aF = F/M, alpha = I^-1 tau about c).

@@ -314,19 +314,20 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
       sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
     }
   }
+  // centroid, P and L: compensated warp sums (pairs s + lo)
+  float lx[3] = {0.f, 0.f, 0.f}, lP[3] = {0.f, 0.f, 0.f}, lL[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sx[k] = warp_sum(sx[k]);
-    sP[k] = warp_sum(sP[k]);
-    sL[k] = warp_sum(sL[k]);
+    warp_sum_c(sx[k], lx[k]);
+    warp_sum_c(sP[k], lP[k]);
+    warp_sum_c(sL[k], lL[k]);
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) sA[k] = warp_sum(sA[k]);
 
   const float iM = br.inv_mass, M = br.mass;
-  const float3 cA = iM * make_float3(sx[0], sx[1], sx[2]);   // c_bsm - anchor
-  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
-  const float3 Lb = make_float3(sL[0], sL[1], sL[2]) - cross(cA, Pb);
+  const float3 cA = iM * make_float3(cval(sx[0], lx[0]), cval(sx[1], lx[1]), cval(sx[2], lx[2]));   // c_bsm - anchor
+  const BsmMoments bm = bsm_moments(sP, lP, sL, lL, cA);
   // A = sum m (x - c) q^T = sum m (x - a) q^T - (c - a) (sum m q)^T
   float A[9];
   {
@@ -384,22 +385,22 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
       sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
     }
   }
+  float lx2[3] = {0.f, 0.f, 0.f}, lP2[3] = {0.f, 0.f, 0.f}, lL2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sx2[k] = warp_sum(sx2[k]);
-    sP2[k] = warp_sum(sP2[k]);
-    sL2[k] = warp_sum(sL2[k]);
+    warp_sum_c(sx2[k], lx2[k]);
+    warp_sum_c(sP2[k], lP2[k]);
+    warp_sum_c(sL2[k], lL2[k]);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
 
   // momentum enforcement (Sec. III-C): dv = (P_bsm - P_asm)/M,
   // w = I^-1 (L_asm - L_bsm) with I about c_asm
-  const float3 cA2 = iM * make_float3(sx2[0], sx2[1], sx2[2]);   // c_asm - anchor
-  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
-  const float3 La = make_float3(sL2[0], sL2[1], sL2[2]) - cross(cA2, Pa);
+  const float3 cA2 = iM * make_float3(cval(sx2[0], lx2[0]), cval(sx2[1], lx2[1]), cval(sx2[2], lx2[2]));   // c_asm - anchor
+  const float3 Pa = make_float3(cval(sP2[0], lP2[0]), cval(sP2[1], lP2[1]), cval(sP2[2], lP2[2]));
   float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
-  if (!(sp.flags & kNoLinMom)) dv = iM * (Pb - Pa);
+  if (!(sp.flags & kNoLinMom)) dv = iM * momentum_dP(bm, sP2, lP2);
   if (!(sp.flags & kNoAngMom)) {
     // S = sum m r r^T about c_asm
     const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
                 s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
     const float tr = s00 + s11 + s22;
     // I = tr(S) I3 - S
-    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, La - Lb, om);
+    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, momentum_dL(bm, sL2, lL2, cA2, Pa), om);
   }
 
   // (3) apply the uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
@@ -585,9 +586,10 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     const float3 ld = cross(med, vb) + cross(me, vbd);
     tL[0] += ld.x; tL[1] += ld.y; tL[2] += ld.z;
   }
+  float lx[3] = {0.f, 0.f, 0.f}, lP[3] = {0.f, 0.f, 0.f}, lL[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sx[k] = warp_sum(sx[k]); sP[k] = warp_sum(sP[k]); sL[k] = warp_sum(sL[k]);
+    warp_sum_c(sx[k], lx[k]); warp_sum_c(sP[k], lP[k]); warp_sum_c(sL[k], lL[k]);
     tx[k] = warp_sum(tx[k]); tP[k] = warp_sum(tP[k]); tL[k] = warp_sum(tL[k]);
   }
 #pragma unroll
@@ -596,9 +598,9 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     tA[k] = warp_sum(tA[k]);
   }
   const float iM = br.inv_mass, M = br.mass;
-  const float3 cA = iM * make_float3(sx[0], sx[1], sx[2]);
-  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
-  const float3 Lb = make_float3(sL[0], sL[1], sL[2]) - cross(cA, Pb);
+  const float3 cA = iM * make_float3(cval(sx[0], lx[0]), cval(sx[1], lx[1]), cval(sx[2], lx[2]));
+  const BsmMoments bm = bsm_moments(sP, lP, sL, lL, cA);
+  const float3 Pb = bsm_P(bm);
   const float3 cAd = iM * make_float3(tx[0], tx[1], tx[2]);
   const float3 Pbd = make_float3(tP[0], tP[1], tP[2]);
   const float3 Lbd = make_float3(tL[0], tL[1], tL[2]) - cross(cAd, Pb) - cross(cA, Pbd);
@@ -675,9 +677,10 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     tXX[0] += 2.f * med.x * e.x; tXX[1] += med.x * e.y + me.x * xad.y; tXX[2] += med.x * e.z + me.x * xad.z;
     tXX[3] += 2.f * med.y * e.y; tXX[4] += med.y * e.z + me.y * xad.z; tXX[5] += 2.f * med.z * e.z;
   }
+  float lx2[3] = {0.f, 0.f, 0.f}, lP2[3] = {0.f, 0.f, 0.f}, lL2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sx2[k] = warp_sum(sx2[k]); sP2[k] = warp_sum(sP2[k]); sL2[k] = warp_sum(sL2[k]);
+    warp_sum_c(sx2[k], lx2[k]); warp_sum_c(sP2[k], lP2[k]); warp_sum_c(sL2[k], lL2[k]);
     tx2[k] = warp_sum(tx2[k]); tP2[k] = warp_sum(tP2[k]); tL2[k] = warp_sum(tL2[k]);
   }
 #pragma unroll
@@ -685,16 +688,15 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     sXX[k] = warp_sum(sXX[k]);
     tXX[k] = warp_sum(tXX[k]);
   }
-  const float3 cA2 = iM * make_float3(sx2[0], sx2[1], sx2[2]);
-  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
-  const float3 La = make_float3(sL2[0], sL2[1], sL2[2]) - cross(cA2, Pa);
+  const float3 cA2 = iM * make_float3(cval(sx2[0], lx2[0]), cval(sx2[1], lx2[1]), cval(sx2[2], lx2[2]));
+  const float3 Pa = make_float3(cval(sP2[0], lP2[0]), cval(sP2[1], lP2[1]), cval(sP2[2], lP2[2]));
   const float3 cA2d = iM * make_float3(tx2[0], tx2[1], tx2[2]);
   const float3 Pad = make_float3(tP2[0], tP2[1], tP2[2]);
   const float3 Lad = make_float3(tL2[0], tL2[1], tL2[2]) - cross(cA2d, Pa) - cross(cA2, Pad);
   float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
   float3 dvd = dv, omd = om;
   if (!(sp.flags & kNoLinMom)) {
-    dv = iM * (Pb - Pa);
+    dv = iM * momentum_dP(bm, sP2, lP2);
     dvd = iM * (Pbd - Pad);
   }
   if (!(sp.flags & kNoAngMom)) {
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
                 s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
                 s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
     const float tr = s00 + s11 + s22;
-    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, La - Lb, om);
+    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, momentum_dL(bm, sL2, lL2, cA2, Pa), om);
     // dS = dSXX - M (c' c^T + c c'^T) ; dI = tr(dS) I3 - dS
     const float d00 = tXX[0] - 2.f * M * cA2d.x * cA2.x;
     const float d01 = tXX[1] - M * (cA2d.x * cA2.y + cA2.x * cA2d.y);
@@ -821,17 +823,19 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
     const float3 l = cross(me, vb);
     sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
   }
+  float lx[3] = {0.f, 0.f, 0.f}, lP[3] = {0.f, 0.f, 0.f}, lL[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sx[k] = warp_sum(sx[k]);
-    sP[k] = warp_sum(sP[k]);
-    sL[k] = warp_sum(sL[k]);
+    warp_sum_c(sx[k], lx[k]);
+    warp_sum_c(sP[k], lP[k]);
+    warp_sum_c(sL[k], lL[k]);
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) sA[k] = warp_sum(sA[k]);
   const float iM = br.inv_mass, M = br.mass;
-  const float3 cA = iM * make_float3(sx[0], sx[1], sx[2]);
-  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
+  const float3 cA = iM * make_float3(cval(sx[0], lx[0]), cval(sx[1], lx[1]), cval(sx[2], lx[2]));
+  const BsmMoments bm = bsm_moments(sP, lP, sL, lL, cA);
+  const float3 Pb = bsm_P(bm);
   float A[9];
   {
     const float qs[3] = {br.qsx, br.qsy, br.qsz};
@@ -866,24 +870,23 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
     sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
     sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
   }
+  float lx2[3] = {0.f, 0.f, 0.f}, lP2[3] = {0.f, 0.f, 0.f}, lL2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sx2[k] = warp_sum(sx2[k]);
-    sP2[k] = warp_sum(sP2[k]);
-    sL2[k] = warp_sum(sL2[k]);
+    warp_sum_c(sx2[k], lx2[k]);
+    warp_sum_c(sP2[k], lP2[k]);
+    warp_sum_c(sL2[k], lL2[k]);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
-  const float3 cA2 = iM * make_float3(sx2[0], sx2[1], sx2[2]);
-  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
-  const float3 Lb = make_float3(sL[0], sL[1], sL[2]) - cross(cA, Pb);
-  const float3 La = make_float3(sL2[0], sL2[1], sL2[2]) - cross(cA2, Pa);
+  const float3 cA2 = iM * make_float3(cval(sx2[0], lx2[0]), cval(sx2[1], lx2[1]), cval(sx2[2], lx2[2]));
+  const float3 Pa = make_float3(cval(sP2[0], lP2[0]), cval(sP2[1], lP2[1]), cval(sP2[2], lP2[2]));
   const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
               s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
               s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
   const float trI = s00 + s11 + s22;
   float3 om = make_float3(0.f, 0.f, 0.f);
-  if (angm) solve_sym3(trI - s00, -s01, -s02, trI - s11, -s12, trI - s22, La - Lb, om);
+  if (angm) solve_sym3(trI - s00, -s01, -s02, trI - s11, -s12, trI - s22, momentum_dL(bm, sL2, lL2, cA2, Pa), om);
 
   // ---- backward: corrections -> dv~, w~ ----
   float sdv[3] = {0.f, 0.f, 0.f}, sw[3] = {0.f, 0.f, 0.f};

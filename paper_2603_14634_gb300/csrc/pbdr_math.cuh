@@ -185,5 +185,93 @@ __device__ __forceinline__ void solve_sym3(float s00, float s01, float s02, floa
   solve_spd3(s00, s01, s02, s11, s12, s22, g, u, 1e-6f);
 }
 
+// ---------------------------------------------------------------------------
+// Compensated body sums.  The momentum constraint (Sec. III-C, Eqs.
+// lin_momentum / ang_momentum) restores P and L from the difference of two
+// body sums taken a pass apart, so FP32 rounding of those sums is what FP32
+// leaves of the conservation.  The centroid, P and L sums are therefore carried
+// as unevaluated pairs s + lo: every addition of two partial sums is split by
+// Knuth's TwoSum into the rounded sum and its exact rounding error, which is
+// kept in lo.  The intrinsics fix the operations (no contraction), and TwoSum's
+// error term is unique, so both partners of a butterfly step get the same pair.
+// ---------------------------------------------------------------------------
+
+// a + b = s + e exactly (Knuth, The Art of Computer Programming vol. 2, 4.2.2)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, lo) <- (s, lo) + (s2, lo2)
+__device__ __forceinline__ void cadd(float &s, float &lo, float s2, float lo2) {
+  float e;
+  two_sum(s, s2, s, e);
+  lo = __fadd_rn(__fadd_rn(lo, lo2), e);
+}
+
+// butterfly warp sum of a compensated value; every lane ends with the same pair
+__device__ __forceinline__ void warp_sum_c(float &s, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    cadd(s, lo, s2, l2);
+  }
+}
+
+__device__ __forceinline__ float cval(float s, float lo) { return __fadd_rn(s, lo); }
+
+// (a_s + a_l) - (b_s + b_l) with the two large parts subtracted first (exact
+// when they are within a factor of two, as two sums a pass apart are)
+__device__ __forceinline__ float cdiff(float as, float al, float bs, float bl) {
+  return __fadd_rn(__fsub_rn(as, bs), __fsub_rn(al, bl));
+}
+
+__device__ __forceinline__ float3 cross_rn(float3 a, float3 b) {
+  return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
+                     __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+                     __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+// First-pass (X_bsm, V_bsm) quantities of a body kept for the momentum step:
+// P_bsm as a pair, the anchor-relative L sum's large part, and
+// lo(L sum) - (c_bsm - a) x P_bsm, so that L_bsm = Ls + T.
+struct BsmMoments {
+  float3 Ps, Pl, Ls, T;
+};
+
+__device__ __forceinline__ BsmMoments bsm_moments(const float *Ps, const float *Pl, const float *Ls,
+                                                  const float *Ll, float3 cA) {
+  BsmMoments r;
+  r.Ps = make_float3(Ps[0], Ps[1], Ps[2]);
+  r.Pl = make_float3(Pl[0], Pl[1], Pl[2]);
+  r.Ls = make_float3(Ls[0], Ls[1], Ls[2]);
+  const float3 P = make_float3(cval(Ps[0], Pl[0]), cval(Ps[1], Pl[1]), cval(Ps[2], Pl[2]));
+  const float3 cp = cross_rn(cA, P);
+  r.T = make_float3(__fsub_rn(Ll[0], cp.x), __fsub_rn(Ll[1], cp.y), __fsub_rn(Ll[2], cp.z));
+  return r;
+}
+
+__device__ __forceinline__ float3 bsm_P(const BsmMoments &b) {
+  return make_float3(cval(b.Ps.x, b.Pl.x), cval(b.Ps.y, b.Pl.y), cval(b.Ps.z, b.Pl.z));
+}
+
+// P_bsm - P_asm from the pairs
+__device__ __forceinline__ float3 momentum_dP(const BsmMoments &b, const float *Pas, const float *Pal) {
+  return make_float3(cdiff(b.Ps.x, b.Pl.x, Pas[0], Pal[0]), cdiff(b.Ps.y, b.Pl.y, Pas[1], Pal[1]),
+                     cdiff(b.Ps.z, b.Pl.z, Pas[2], Pal[2]));
+}
+
+// L_asm - L_bsm, both about their own centre of mass: L = (anchor-relative
+// sum) - (c - a) x P; the large parts of the two sums are subtracted first
+__device__ __forceinline__ float3 momentum_dL(const BsmMoments &b, const float *Las, const float *Lal,
+                                              float3 cA2, float3 Pa) {
+  const float3 cp = cross_rn(cA2, Pa);
+  const float3 Ta = make_float3(__fsub_rn(Lal[0], cp.x), __fsub_rn(Lal[1], cp.y), __fsub_rn(Lal[2], cp.z));
+  return make_float3(__fadd_rn(__fsub_rn(Las[0], b.Ls.x), __fsub_rn(Ta.x, b.T.x)),
+                     __fadd_rn(__fsub_rn(Las[1], b.Ls.y), __fsub_rn(Ta.y, b.T.y)),
+                     __fadd_rn(__fsub_rn(Las[2], b.Ls.z), __fsub_rn(Ta.z, b.T.z)));
+}
+
 }  // namespace
 }  // namespace pbdr
