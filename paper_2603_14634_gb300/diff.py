@@ -79,25 +79,29 @@ def com_jacobian(ctx, scene, steps: int, seeds: List, stream=None,
     final = None
     for at in range(0, len(seeds), batch):
         group = seeds[at:at + batch]
-        ids = [ctx.create_scene(scene) for _ in group]
-        for sid, dv in zip(ids, group):
-            if isinstance(dv, str):
-                ctx.write_tangent(sid, None, None, stream)
-                ctx.write_tangent_friction(sid, 1.0, stream)
-            else:
-                ctx.write_tangent(sid, None, np.asarray(dv, np.float32), stream)
-        ctx.step_tangent(ids, steps, stream)
-        for j, sid in enumerate(ids):
-            dpos, _ = ctx.read_tangent(sid, stream)
-            dp = dpos.astype(np.float64)
-            J[:, at + j] = np.concatenate([(m[s, None] * dp[s]).sum(0) / m[s].sum() for s in sl])
-            if final is None:
-                pos, _, err = ctx.read_state(sid, stream)
-                if err:
-                    raise RuntimeError(f"device error bits {err}")
-                final = body_coms(scene, pos)
-        for sid in ids:
-            ctx.destroy_scene(sid)
+        ids = []
+        try:
+            for _ in group:
+                ids.append(ctx.create_scene(scene))
+            for sid, dv in zip(ids, group):
+                if isinstance(dv, str):
+                    ctx.write_tangent(sid, None, None, stream)
+                    ctx.write_tangent_friction(sid, 1.0, stream)
+                else:
+                    ctx.write_tangent(sid, None, np.asarray(dv, np.float32), stream)
+            ctx.step_tangent(ids, steps, stream)
+            for j, sid in enumerate(ids):
+                dpos, _ = ctx.read_tangent(sid, stream)
+                dp = dpos.astype(np.float64)
+                J[:, at + j] = np.concatenate([(m[s, None] * dp[s]).sum(0) / m[s].sum() for s in sl])
+                if final is None:
+                    pos, _, err = ctx.read_state(sid, stream)
+                    if err:
+                        raise RuntimeError(f"device error bits {err}")
+                    final = body_coms(scene, pos)
+        finally:
+            for sid in ids:
+                ctx.destroy_scene(sid)
     return final, J
 
 
@@ -142,6 +146,21 @@ def rigid_gradient(scene, vbar0: np.ndarray) -> np.ndarray:
     return out
 
 
+def final_com(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps: int, stream=None) -> np.ndarray:
+    """Final centres of mass [B, 3] of the scene started with per-body rigid
+    velocities (v_lin, w_ang), by plain substeps."""
+    sc = _with_velocity(scene, rigid_velocity(scene, v_lin, w_ang))
+    sid = ctx.create_scene(sc)
+    try:
+        ctx.step(sid, steps, stream)
+        pos, _, err = ctx.read_state(sid, stream)
+        if err:
+            raise RuntimeError(f"device error bits {err}")
+    finally:
+        ctx.destroy_scene(sid)
+    return body_coms(sc, pos)
+
+
 def com_gradient_reverse(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps: int,
                          weights: np.ndarray, checkpoint_every: int = 20,
                          stream=None, with_mu: bool = False):
@@ -153,14 +172,16 @@ def com_gradient_reverse(ctx, scene, v_lin: np.ndarray, w_ang: np.ndarray, steps
     call adjoint."""
     sc = _with_velocity(scene, rigid_velocity(scene, v_lin, w_ang))
     sid = ctx.create_scene(sc)
-    ctx.write_adjoint(sid, com_loss_adjoint(sc, weights).astype(np.float32), None, stream)
-    ctx.adjoint(sid, steps, checkpoint_every, stream)
-    pos, _, err = ctx.read_state(sid, stream)
-    if err:
-        raise RuntimeError(f"device error bits {err}")
-    _, vbar0 = ctx.read_adjoint(sid, stream)
-    mubar = ctx.read_adjoint_friction(sid, stream) if with_mu else None
-    ctx.destroy_scene(sid)
+    try:
+        ctx.write_adjoint(sid, com_loss_adjoint(sc, weights).astype(np.float32), None, stream)
+        ctx.adjoint(sid, steps, checkpoint_every, stream)
+        pos, _, err = ctx.read_state(sid, stream)
+        if err:
+            raise RuntimeError(f"device error bits {err}")
+        _, vbar0 = ctx.read_adjoint(sid, stream)
+        mubar = ctx.read_adjoint_friction(sid, stream) if with_mu else None
+    finally:
+        ctx.destroy_scene(sid)
     if with_mu:
         return body_coms(sc, pos), rigid_gradient(sc, vbar0), mubar
     return body_coms(sc, pos), rigid_gradient(sc, vbar0)
@@ -185,7 +206,8 @@ try:   # the autograd wrapper needs torch; the rest of the module does not
                 final, J = final_com_and_jacobian(ctx, scene, v, w, int(steps))
                 fctx.save_for_backward(torch.from_numpy(J))
             elif mode == "reverse":
-                final, _ = com_gradient_reverse(ctx, scene, v, w, int(steps), np.zeros((fctx.B, 3)))
+                # primal only; the one adjoint run happens in backward
+                final = final_com(ctx, scene, v, w, int(steps))
                 fctx.args = (ctx, scene, v, w, int(steps))
             else:
                 raise ValueError("mode is 'forward' or 'reverse'")

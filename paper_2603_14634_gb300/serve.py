@@ -15,8 +15,12 @@ admitted scene resident on the device and runs in ticks; every tick it
    their final states in one call and destroys their scenes, which frees
    their device ranges for later requests.
 
-Latency of a request = completion time - arrival time (wall clock); the tick
-latency is the time of one batched substep of all resident requests.
+Latency of a request = completion time - arrival time (wall clock), where
+completion is when its final state has been copied back to the host.  The
+tick latency is the device time of one batched substep of all resident
+requests (CUDA events around the step on the serving stream).  The host runs
+at most one batched substep ahead of the device: before a tick ends it waits
+for the previous tick's substep, so admission sees the device's progress.
 """
 from __future__ import annotations
 
@@ -30,6 +34,27 @@ import numpy as np
 # device bytes held per resident particle (state, rest offsets, neighbour
 # lists, scratch and plan buffers), used by the admission ledger
 BYTES_PER_PARTICLE = 320
+
+
+class CudaTimingEvent:
+    """A CUDA timing event recorded on a stream given as a torch stream, a
+    raw ``cudaStream_t`` value or None (the current stream)."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.ev = torch.cuda.Event(enable_timing=True)
+
+    def record(self, stream=None):
+        if isinstance(stream, int):
+            stream = self._torch.cuda.ExternalStream(stream) if stream else None
+        self.ev.record(stream)
+
+    def synchronize(self):
+        self.ev.synchronize()
+
+    def elapsed_time(self, end: "CudaTimingEvent") -> float:
+        return self.ev.elapsed_time(end.ev)
 
 
 @dataclasses.dataclass
@@ -48,13 +73,20 @@ class Server:
     """Continuous batching over a ``binding.Context``-like object.
 
     ``ctx_factory`` builds the context (a fake one in host-only tests);
-    ``clock`` returns seconds (``time.perf_counter`` by default).
+    ``clock`` returns seconds (``time.perf_counter`` by default);
+    ``event_factory`` returns a timing event with ``record(stream)``,
+    ``synchronize()`` and ``elapsed_time(end)`` in ms (CUDA events of the
+    serving stream by default; with a fake context and no factory, ticks are
+    timed on the host clock).
     """
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, device: int = 0,
                  ctx_factory: Optional[Callable[[], object]] = None,
                  clock: Callable[[], float] = time.perf_counter, stream=None,
-                 bytes_per_particle: int = BYTES_PER_PARTICLE):
+                 bytes_per_particle: int = BYTES_PER_PARTICLE,
+                 event_factory: Optional[Callable[[], object]] = None):
+        if event_factory is None and ctx_factory is None:
+            event_factory = CudaTimingEvent
         if ctx_factory is None:
             from .binding import Context, OPT_AUTOTUNE, OPT_GRAPHS
 
@@ -74,6 +106,8 @@ class Server:
         self.finished: List[Request] = []
         self.results: Dict[int, tuple] = {}
         self.ledger = 0
+        self.event_factory = event_factory
+        self._inflight: collections.deque = collections.deque()   # (start, end) events per tick
         self.tick_ms: List[float] = []
         self.host_ms = {"admit": 0.0, "step": 0.0, "retire": 0.0}
         self.ticks = 0
@@ -126,11 +160,12 @@ class Server:
             n += 1
         return n
 
-    def _retire(self, now: float):
+    def _retire(self):
         done = self._due.pop(self._stepped, [])   # in admission order
         if not done:
             return
         pos, vel, err = self.ctx.read_states([r.sid for r in done], stream=self.stream)
+        now = self.clock() - self.t0              # the results are on the host now
         at = 0
         for k, req in enumerate(done):
             n = int(req.scene.num_particles)
@@ -145,6 +180,14 @@ class Server:
             self.finished.append(req)
 
     # ---- main loop -----------------------------------------------------------
+    def _drain(self, keep: int):
+        """Waits until at most `keep` batched substeps are in flight and
+        records the device time of the finished ones."""
+        while len(self._inflight) > keep:
+            ev0, ev1 = self._inflight.popleft()
+            ev1.synchronize()
+            self.tick_ms.append(float(ev0.elapsed_time(ev1)))
+
     def tick(self) -> bool:
         """One batched substep + admission + retirement round; False when idle."""
         t_0 = self.clock()
@@ -153,20 +196,29 @@ class Server:
             if self._ids_dirty:
                 self._ids = [r.sid for r in self.active.values()]
                 self._ids_dirty = False
-            self.ctx.step(self._ids, 1, self.stream)   # asynchronous
+            if self.event_factory is not None:
+                ev0, ev1 = self.event_factory(), self.event_factory()
+                ev0.record(self.stream)
+                self.ctx.step(self._ids, 1, self.stream)   # asynchronous
+                ev1.record(self.stream)
+                self._inflight.append((ev0, ev1))
+            else:
+                self.ctx.step(self._ids, 1, self.stream)
             self._stepped += 1
             self.work_done += self._tick_work
         t_a = self.clock()
         self._admit(t_a - self.t0)                 # host work overlaps the substep
         t_b = self.clock()
-        self._retire(t_b - self.t0)                # reads back finished ones (synchronises)
+        self._retire()                             # reads back finished ones (synchronises)
+        self._drain(keep=1)                        # at most one substep ahead of the device
         t_c = self.clock()
         if not stepped:
             return bool(self.pending or self.active)
         self.host_ms["step"] += (t_a - t_0) * 1e3
         self.host_ms["admit"] += (t_b - t_a) * 1e3
         self.host_ms["retire"] += (t_c - t_b) * 1e3
-        self.tick_ms.append((t_c - t_0) * 1e3)
+        if self.event_factory is None:
+            self.tick_ms.append((t_c - t_0) * 1e3)
         self.ticks += 1
         return True
 
@@ -188,6 +240,7 @@ class Server:
                         time.sleep(min(wait, 0.05))
                     continue
             self.tick()
+        self._drain(keep=0)
         return self.stats()
 
     def stats(self) -> dict:
