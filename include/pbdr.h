@@ -319,9 +319,10 @@ int pbdr_read_profile(pbdr_ctx *ctx, double *stage_ms, int64_t *stage_launches, 
  *   sorted_key [n] device out: bucket in [0, T), T = smallest power of two >= 2n
  *   sorted_id  [n] device out: particle indices sorted by key, ascending within a key
  *   nbr_cnt    [n] device out: full neighbour count of each particle; a count
- *              above cap means the list was cut at cap entries
- *   nbr        [cap*n] device out: ascending neighbour indices, column-major
- *              (slot j of particle p at nbr[j*n + p])
+ *              above cap means the list was cut to its cap lowest indices
+ *   nbr        [cap*n] device out: ascending neighbour indices (the lowest
+ *              min(count, cap) of them), column-major (slot j of particle p
+ *              at nbr[j*n + p])
  *   cap        1..64
  *   stream     cudaStream_t (NULL = legacy default stream); asynchronous
  *

@@ -124,41 +124,6 @@ __device__ __forceinline__ void warp_sums(float *v, int lane) {
   halve<N4, N5, 1>(v, lane);
 }
 
-// The same recursive halving for compensated values (pairs v + l, see
-// cadd): each step adds the partner's pair with TwoSum, so afterwards lane
-// l holds the pair of value ws_index(V, l) in (v[0], l[0]).
-template <int N, int H, int D>
-__device__ __forceinline__ void halve_c(float *v, float *l, int lane) {
-  if (N == 1) {
-    const float s2 = __shfl_xor_sync(kFull, v[0], D), l2 = __shfl_xor_sync(kFull, l[0], D);
-    cadd(v[0], l[0], s2, l2);
-    return;
-  }
-  const bool up = (lane & D) != 0;
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    const float vlo = v[k], llo = l[k];
-    const float vhi = (k + H < N) ? v[k + H] : 0.f, lhi = (k + H < N) ? l[k + H] : 0.f;
-    const float rs = __shfl_xor_sync(kFull, up ? vlo : vhi, D);
-    const float rl = __shfl_xor_sync(kFull, up ? llo : lhi, D);
-    v[k] = up ? vhi : vlo;
-    l[k] = up ? lhi : llo;
-    cadd(v[k], l[k], rs, rl);
-  }
-}
-
-template <int V>
-__device__ __forceinline__ void warp_sums_c(float *v, float *l, int lane) {
-  static_assert(V >= 1 && V <= 32, "one value per lane at most");
-  constexpr int N0 = V, N1 = (N0 + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2, N4 = (N3 + 1) / 2,
-                N5 = (N4 + 1) / 2;
-  halve_c<N0, N1, 16>(v, l, lane);
-  halve_c<N1, N2, 8>(v, l, lane);
-  halve_c<N2, N3, 4>(v, l, lane);
-  halve_c<N3, N4, 2>(v, l, lane);
-  halve_c<N4, N5, 1>(v, l, lane);
-}
-
 __device__ __forceinline__ void quat_mat(float4 q, float *R) {
   const float x = q.x, y = q.y, z = q.z, w = q.w;
   R[0] = 1.f - 2.f * (y * y + z * z);
@@ -546,10 +511,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           const int32_t i = l0 + lane + 32 * j;
           if (i < l1) q4[j] = __ldg(a.Q + p0 + i);
         }
-        // first sums: plain A (9) and compensated centroid, P, L (9)
-        float red[9], cs[9], cl[9];
+        // first sums: centroid (3) and A (9)
+        float red[12];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) red[k] = cs[k] = cl[k] = 0.f;
+        for (int k = 0; k < 12; ++k) red[k] = 0.f;
 #pragma unroll
         for (int j = 0; j < kChunk / 32; ++j) {
           const int32_t i = l0 + lane + 32 * j;
@@ -585,36 +550,15 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
             dX = add(dX, acc);
           }
           DX[i] = make_float4(dX.x, dX.y, dX.z, 0.f);
-          const float3 xb = add(f3(xp), dX);
-          float3 vb;
-          if (std_vel)   // uniform per scene
-            vb = mul(idt, sub(xb, f3(a.X[p])));
-          else
-            vb = add(f3(vp), mul(idt, dX));
-          const float4 q = q4[j];
-          const float m = q.w;
-          const float3 e = sub(xb, anc);
-          const float3 me = mul(m, e);
-          cs[0] += me.x; cs[1] += me.y; cs[2] += me.z;
-          red[0] += me.x * q.x; red[1] += me.x * q.y; red[2] += me.x * q.z;
-          red[3] += me.y * q.x; red[4] += me.y * q.y; red[5] += me.y * q.z;
-          red[6] += me.z * q.x; red[7] += me.z * q.y; red[8] += me.z * q.z;
-          cs[3] += m * vb.x; cs[4] += m * vb.y; cs[5] += m * vb.z;
-          const float3 l = cross3(me, vb);
-          cs[6] += l.x; cs[7] += l.y; cs[8] += l.z;
+          const float3 xb = add(f3(xp), dX);   // X_bsm (V_bsm is formed by the owner)
+          shape_terms(red, q4[j].w, sub(xb, anc), q4[j]);
         }
-        warp_sums<9>(red, lane);
-        warp_sums_c<9>(cs, cl, lane);
+        warp_sums<12>(red, lane);
         {
-          // slot: A (9) | centroid, P, L large parts (9) | their lo parts (9)
-          const int k = ws_index(9, lane);
+          const int k = ws_index(12, lane);
           float *pt = part_local ? part_sm + kPartialFloats * (br.slot0 - slot_base + C.k)
                                  : a.partials + (size_t)kPartialFloats * (br.slot0 + C.k);
-          if (k >= 0) {
-            pt[k] = red[0];
-            pt[9 + k] = cs[0];
-            pt[18 + k] = cl[0];
-          }
+          if (k >= 0) pt[k] = red[0];
         }
       }
       __syncthreads();   // every contact of this iteration has read X_i
@@ -623,52 +567,31 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
         const BodyRec br = a.bodies[b];
         float4 *rp = rotp(b - b0), *ap = ancp(b - b0);
         const float3 anc = f3(*ap);
-        // first sums: the chunks' partials in chunk order (lane j < 9 adds A
-        // value j, lane 9 + j the pair of compensated value j)
-        float red1[9], c1s[9], c1l[9];
+        // first sums: the chunks' partials in chunk order (lane j adds value j)
+        float red1[12];
         {
-          float ms = 0.f, ml = 0.f;
-          if (lane < 18) {
+          float mine = 0.f;
+          if (lane < 12) {
             const float *pt = (part_local ? part_sm + kPartialFloats * (br.slot0 - slot_base)
                                           : a.partials + (size_t)kPartialFloats * br.slot0) + lane;
-            ms = pt[0];
-            if (lane >= 9) {
-              ml = pt[9];
-              for (int k = 1; k < br.nk; ++k) cadd(ms, ml, pt[(size_t)kPartialFloats * k], pt[(size_t)kPartialFloats * k + 9]);
-            } else {
-              for (int k = 1; k < br.nk; ++k) ms += pt[(size_t)kPartialFloats * k];
-            }
+            mine = pt[0];
+            for (int k = 1; k < br.nk; ++k) mine += pt[(size_t)kPartialFloats * k];
           }
 #pragma unroll
-          for (int j = 0; j < 9; ++j) {
-            red1[j] = __shfl_sync(kFull, ms, j);
-            c1s[j] = __shfl_sync(kFull, ms, 9 + j);
-            c1l[j] = __shfl_sync(kFull, ml, 9 + j);
-          }
+          for (int j = 0; j < 12; ++j) red1[j] = __shfl_sync(kFull, mine, j);
         }
         const float M = br.mass, iM = br.inv_mass;
-        const float3 cA = mul(iM, make_float3(cval(c1s[0], c1l[0]), cval(c1s[1], c1l[1]), cval(c1s[2], c1l[2])));
-        const BsmMoments bm = bsm_moments(c1s + 3, c1l + 3, c1s + 6, c1l + 6, cA);
         float Am[9];
-        {
-          const float qs[3] = {br.qsx, br.qsy, br.qsz};
-          const float ca[3] = {cA.x, cA.y, cA.z};
-#pragma unroll
-          for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) Am[3 * rr + cc] = red1[3 * rr + cc] - ca[rr] * qs[cc];
-        }
+        const float3 cA = shape_matrix(red1, iM, br.qsx, br.qsy, br.qsz, Am);
         const float4 qrot = shape_rotation(Am, *rp);
         float R[9];
         quat_mat(qrot, R);
         // goals g = R q + c -> X_asm, V_asm; second sums
         const int32_t l0 = br.start - p0, l1 = l0 + br.count;
-        // second sums: compensated centroid, P, L (9) and plain sum m r r^T (6)
-        float cs[9], cl[9], red[6];
+        // the sums of the momentum step (momentum_terms)
+        float red[kMomentumSums];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) cs[k] = cl[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[k] = 0.f;
+        for (int k = 0; k < kMomentumSums; ++k) red[k] = 0.f;
         for (int32_t i = l0 + lane; i < l1; i += 32) {
           const int32_t p = p0 + i;
           const float4 xi = Xs[i];
@@ -692,39 +615,17 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) k_scene_substep(Fused
           const float3 va = std_vel ? mul(idt, sub(xa, xinit)) : add(vb, mul(idt, dsm));
           DX[i] = make_float4(xa.x, xa.y, xa.z, 0.f);
           Vl[i] = make_float4(va.x, va.y, va.z, 0.f);
-          const float3 e = sub(xa, anc);
-          const float3 me = mul(m, e);
-          cs[0] += me.x; cs[1] += me.y; cs[2] += me.z;
-          cs[3] += m * va.x; cs[4] += m * va.y; cs[5] += m * va.z;
-          const float3 l = cross3(me, va);
-          cs[6] += l.x; cs[7] += l.y; cs[8] += l.z;
-          red[0] += me.x * e.x; red[1] += me.x * e.y; red[2] += me.x * e.z;
-          red[3] += me.y * e.y; red[4] += me.y * e.z; red[5] += me.z * e.z;
+          momentum_terms(red, m, sub(sub(xb, anc), cA), xb, vb, xa, va, sub(xa, anc));
         }
-        warp_sums_c<9>(cs, cl, lane);
-        warp_sums<6>(red, lane);
+        warp_sums<kMomentumSums>(red, lane);
         {
-          const float t0 = cs[0], u0 = cl[0], r0 = red[0];
+          const float t0 = red[0];
 #pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            cs[k] = __shfl_sync(kFull, t0, ws_lane(9, k));
-            cl[k] = __shfl_sync(kFull, u0, ws_lane(9, k));
-          }
-#pragma unroll
-          for (int k = 0; k < 6; ++k) red[k] = __shfl_sync(kFull, r0, ws_lane(6, k));
+          for (int k = 0; k < kMomentumSums; ++k) red[k] = __shfl_sync(kFull, t0, ws_lane(kMomentumSums, k));
         }
         // momentum enforcement (Sec. III-C)
-        const float3 cA2 = mul(iM, make_float3(cval(cs[0], cl[0]), cval(cs[1], cl[1]), cval(cs[2], cl[2])));
-        const float3 Pa = make_float3(cval(cs[3], cl[3]), cval(cs[4], cl[4]), cval(cs[5], cl[5]));
-        float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
-        if (!(sp.flags & kNoLinMom)) dv = mul(iM, momentum_dP(bm, cs + 3, cl + 3));
-        if (!(sp.flags & kNoAngMom)) {
-          const float s00 = red[0] - M * cA2.x * cA2.x, s01 = red[1] - M * cA2.x * cA2.y,
-                      s02 = red[2] - M * cA2.x * cA2.z, s11 = red[3] - M * cA2.y * cA2.y,
-                      s12 = red[4] - M * cA2.y * cA2.z, s22 = red[5] - M * cA2.z * cA2.z;
-          const float tr = s00 + s11 + s22;
-          solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, momentum_dL(bm, cs + 6, cl + 6, cA2, Pa), om);
-        }
+        float3 cA2, dv, om;
+        momentum_step(red, cA, M, iM, !(sp.flags & kNoLinMom), !(sp.flags & kNoAngMom), cA2, dv, om);
         bool bad = false;
         for (int32_t i = l0 + lane; i < l1; i += 32) {
           const float3 xa = f3(DX[i]);

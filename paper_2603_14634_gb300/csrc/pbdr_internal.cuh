@@ -59,7 +59,7 @@ struct alignas(16) Chunk {
   int32_t k;                    // index of the chunk within its body
 };
 constexpr int kBodyScratch = 12;    // float4 per body in FusedArgs::biter
-constexpr int kPartialFloats = 28;  // floats per partial-sum slot: 9 plain sums, 9 pairs
+constexpr int kPartialFloats = 12;  // floats per partial-sum slot: centroid (3), A (9)
 
 // Per-body external wrench, set by the host (force, torque) and the
 // per-substep derived accelerations (aF = F/M, alpha = I^-1 tau about c).

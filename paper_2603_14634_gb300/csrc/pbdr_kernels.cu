@@ -270,7 +270,9 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
   const float3 anc = f3(a.bcom[b]);
 
   // (1) contacts from X_i (Jacobi) -> X_bsm, V_bsm ; first body reduction
-  float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
+  float s1[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s1[k] = 0.f;
   // Each lane takes particles p0 + lane + 32 j in order of j; the loads of
   // kIterBatch of them are issued together (X_in, V_in, Q and the list
   // lengths are read-only here), so one memory round trip covers a batch.
@@ -301,50 +303,24 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
         vb = f3(vp) + idt * dX;   // V_i + dX/dt (Sec. III-B)
       a.Xout[p] = make_float4(xb.x, xb.y, xb.z, xp.w);
       a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
-      const float4 q = qr[u];
-      const float m = q.w;
-      const float3 e = xb - anc;
-      const float3 me = m * e;
-      sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
-      sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
-      sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
-      sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
-      sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
-      const float3 l = cross(me, vb);
-      sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
+      shape_terms(s1, qr[u].w, xb - anc, qr[u]);
     }
   }
-  // centroid, P and L: compensated warp sums (pairs s + lo)
-  float lx[3] = {0.f, 0.f, 0.f}, lP[3] = {0.f, 0.f, 0.f}, lL[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    warp_sum_c(sx[k], lx[k]);
-    warp_sum_c(sP[k], lP[k]);
-    warp_sum_c(sL[k], lL[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < 9; ++k) sA[k] = warp_sum(sA[k]);
+  for (int k = 0; k < 12; ++k) s1[k] = warp_sum(s1[k]);
 
   const float iM = br.inv_mass, M = br.mass;
-  const float3 cA = iM * make_float3(cval(sx[0], lx[0]), cval(sx[1], lx[1]), cval(sx[2], lx[2]));   // c_bsm - anchor
-  const BsmMoments bm = bsm_moments(sP, lP, sL, lL, cA);
-  // A = sum m (x - c) q^T = sum m (x - a) q^T - (c - a) (sum m q)^T
   float A[9];
-  {
-    const float qs[3] = {br.qsx, br.qsy, br.qsz};
-    const float ca[3] = {cA.x, cA.y, cA.z};
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
-  }
+  const float3 cA = shape_matrix(s1, iM, br.qsx, br.qsy, br.qsz, A);   // c_bsm - anchor
   const float4 qrot = shape_rotation(A, a.quat[b]);
   float R[9];
   quat_to_mat(qrot, R);
 
-  // (2) shape-matching goals g = R q + c -> X_asm, V_asm ; second reduction
-  float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f};
-  float sXX[6] = {0.f};
+  // (2) shape-matching goals g = R q + c -> X_asm, V_asm ; the sums of the
+  // momentum step (momentum_terms)
+  float sm[kMomentumSums];
+#pragma unroll
+  for (int k = 0; k < kMomentumSums; ++k) sm[k] = 0.f;
   for (int32_t pb = p0 + lane; pb < pe; pb += 32 * kIterBatch) {
     float4 xr[kIterBatch], vr[kIterBatch], qr[kIterBatch];
 #pragma unroll
@@ -375,41 +351,16 @@ __global__ void __launch_bounds__(128) k_iterate(IterArgs a) {
         va = f3(vb4) + idt * dsm;
       a.Xout[p] = make_float4(xa.x, xa.y, xa.z, xb4.w);
       a.Vout[p] = make_float4(va.x, va.y, va.z, 0.f);
-      const float3 e = xa - anc;
-      const float3 me = m * e;
-      sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
-      sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
-      const float3 l = cross(me, va);
-      sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
-      sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
-      sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
+      momentum_terms(sm, m, f3(xb4) - anc - cA, f3(xb4), f3(vb4), xa, va, xa - anc);
     }
   }
-  float lx2[3] = {0.f, 0.f, 0.f}, lP2[3] = {0.f, 0.f, 0.f}, lL2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    warp_sum_c(sx2[k], lx2[k]);
-    warp_sum_c(sP2[k], lP2[k]);
-    warp_sum_c(sL2[k], lL2[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
+  for (int k = 0; k < kMomentumSums; ++k) sm[k] = warp_sum(sm[k]);
 
   // momentum enforcement (Sec. III-C): dv = (P_bsm - P_asm)/M,
   // w = I^-1 (L_asm - L_bsm) with I about c_asm
-  const float3 cA2 = iM * make_float3(cval(sx2[0], lx2[0]), cval(sx2[1], lx2[1]), cval(sx2[2], lx2[2]));   // c_asm - anchor
-  const float3 Pa = make_float3(cval(sP2[0], lP2[0]), cval(sP2[1], lP2[1]), cval(sP2[2], lP2[2]));
-  float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
-  if (!(sp.flags & kNoLinMom)) dv = iM * momentum_dP(bm, sP2, lP2);
-  if (!(sp.flags & kNoAngMom)) {
-    // S = sum m r r^T about c_asm
-    const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
-                s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
-                s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
-    const float tr = s00 + s11 + s22;
-    // I = tr(S) I3 - S
-    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, momentum_dL(bm, sL2, lL2, cA2, Pa), om);
-  }
+  float3 cA2, dv, om;
+  momentum_step(sm, cA, M, iM, !(sp.flags & kNoLinMom), !(sp.flags & kNoAngMom), cA2, dv, om);
 
   // (3) apply the uniform corrections: v = v_asm + dv - w x r, x = x_asm + (dv - w x r) dt
   bool bad = false;
@@ -550,8 +501,11 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
   const float dmu = t.dmu ? t.dmu[br.scene] : 0.f;
   const float3 anc = f3(a.bcom[b]);   // a constant reference point: no tangent
 
-  // (1) contacts -> X_bsm, V_bsm and tangents; first sums and their tangents
-  float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
+  // (1) contacts -> X_bsm, V_bsm and tangents; first sums (as k_iterate),
+  // P_bsm for the tangent terms, and the tangents of the sums
+  float s1[12], sP[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s1[k] = 0.f;
   float tx[3] = {0.f, 0.f, 0.f}, tA[9] = {0.f}, tP[3] = {0.f, 0.f, 0.f}, tL[3] = {0.f, 0.f, 0.f};
   for (int32_t p = p0 + lane; p < pe; p += 32) {
     const float4 xp = a.Xin[p], vp = a.Vin[p];
@@ -568,16 +522,10 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     t.Vdout[p] = make_float4(vbd.x, vbd.y, vbd.z, 0.f);
     const float4 q = a.Q[p];
     const float m = q.w;
-    const float3 e = xb - anc;
-    const float3 me = m * e;
+    shape_terms(s1, m, xb - anc, q);
+    const float3 me = m * (xb - anc);
     const float3 med = m * xbd;
-    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
-    sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
-    sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
-    sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
     sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
-    const float3 l = cross(me, vb);
-    sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
     tx[0] += med.x; tx[1] += med.y; tx[2] += med.z;
     tA[0] += med.x * q.x; tA[1] += med.x * q.y; tA[2] += med.x * q.z;
     tA[3] += med.y * q.x; tA[4] += med.y * q.y; tA[5] += med.y * q.z;
@@ -586,35 +534,29 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     const float3 ld = cross(med, vb) + cross(me, vbd);
     tL[0] += ld.x; tL[1] += ld.y; tL[2] += ld.z;
   }
-  float lx[3] = {0.f, 0.f, 0.f}, lP[3] = {0.f, 0.f, 0.f}, lL[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s1[k] = warp_sum(s1[k]);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    warp_sum_c(sx[k], lx[k]); warp_sum_c(sP[k], lP[k]); warp_sum_c(sL[k], lL[k]);
+    sP[k] = warp_sum(sP[k]);
     tx[k] = warp_sum(tx[k]); tP[k] = warp_sum(tP[k]); tL[k] = warp_sum(tL[k]);
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    sA[k] = warp_sum(sA[k]);
-    tA[k] = warp_sum(tA[k]);
-  }
+  for (int k = 0; k < 9; ++k) tA[k] = warp_sum(tA[k]);
   const float iM = br.inv_mass, M = br.mass;
-  const float3 cA = iM * make_float3(cval(sx[0], lx[0]), cval(sx[1], lx[1]), cval(sx[2], lx[2]));
-  const BsmMoments bm = bsm_moments(sP, lP, sL, lL, cA);
-  const float3 Pb = bsm_P(bm);
+  float A[9], Ad[9];
+  const float3 cA = shape_matrix(s1, iM, br.qsx, br.qsy, br.qsz, A);
+  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
   const float3 cAd = iM * make_float3(tx[0], tx[1], tx[2]);
   const float3 Pbd = make_float3(tP[0], tP[1], tP[2]);
   const float3 Lbd = make_float3(tL[0], tL[1], tL[2]) - cross(cAd, Pb) - cross(cA, Pbd);
-  float A[9], Ad[9];
   {
     const float qs[3] = {br.qsx, br.qsy, br.qsz};
-    const float ca[3] = {cA.x, cA.y, cA.z}, cad[3] = {cAd.x, cAd.y, cAd.z};
+    const float cad[3] = {cAd.x, cAd.y, cAd.z};
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
-        Ad[3 * r + c] = tA[3 * r + c] - cad[r] * qs[c];
-      }
+      for (int c = 0; c < 3; ++c) Ad[3 * r + c] = tA[3 * r + c] - cad[r] * qs[c];
   }
   const float4 qrot = shape_rotation(A, a.quat[b]);
   float R[9];
@@ -636,8 +578,11 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     solve_sym3(tr - S[0], -s01, -s02, tr - S[4], -s12, tr - S[8], ax, wr);
   }
 
-  // (2) goals and their tangents; second sums
-  float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f}, sXX[6] = {0.f};
+  // (2) goals and their tangents; the momentum sums (as k_iterate), P_asm for
+  // the tangent terms, and the tangents of the second sums
+  float sm[kMomentumSums], sP2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kMomentumSums; ++k) sm[k] = 0.f;
   float tx2[3] = {0.f, 0.f, 0.f}, tP2[3] = {0.f, 0.f, 0.f}, tL2[3] = {0.f, 0.f, 0.f}, tXX[6] = {0.f};
   for (int32_t p = p0 + lane; p < pe; p += 32) {
     const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
@@ -661,15 +606,11 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     a.Vout[p] = make_float4(va.x, va.y, va.z, 0.f);
     t.Xdout[p] = make_float4(xad.x, xad.y, xad.z, 0.f);
     t.Vdout[p] = make_float4(vad.x, vad.y, vad.z, 0.f);
+    momentum_terms(sm, m, f3(xb4) - anc - cA, f3(xb4), f3(vb4), xa, va, xa - anc);
     const float3 e = xa - anc;
     const float3 me = m * e;
     const float3 med = m * xad;
-    sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
     sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
-    const float3 l = cross(me, va);
-    sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
-    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
-    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
     tx2[0] += med.x; tx2[1] += med.y; tx2[2] += med.z;
     tP2[0] += m * vad.x; tP2[1] += m * vad.y; tP2[2] += m * vad.z;
     const float3 ld = cross(med, va) + cross(me, vad);
@@ -677,34 +618,29 @@ __global__ void __launch_bounds__(128) k_iterate_tangent(IterArgs a, TangentArgs
     tXX[0] += 2.f * med.x * e.x; tXX[1] += med.x * e.y + me.x * xad.y; tXX[2] += med.x * e.z + me.x * xad.z;
     tXX[3] += 2.f * med.y * e.y; tXX[4] += med.y * e.z + me.y * xad.z; tXX[5] += 2.f * med.z * e.z;
   }
-  float lx2[3] = {0.f, 0.f, 0.f}, lP2[3] = {0.f, 0.f, 0.f}, lL2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kMomentumSums; ++k) sm[k] = warp_sum(sm[k]);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    warp_sum_c(sx2[k], lx2[k]); warp_sum_c(sP2[k], lP2[k]); warp_sum_c(sL2[k], lL2[k]);
+    sP2[k] = warp_sum(sP2[k]);
     tx2[k] = warp_sum(tx2[k]); tP2[k] = warp_sum(tP2[k]); tL2[k] = warp_sum(tL2[k]);
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    sXX[k] = warp_sum(sXX[k]);
-    tXX[k] = warp_sum(tXX[k]);
-  }
-  const float3 cA2 = iM * make_float3(cval(sx2[0], lx2[0]), cval(sx2[1], lx2[1]), cval(sx2[2], lx2[2]));
-  const float3 Pa = make_float3(cval(sP2[0], lP2[0]), cval(sP2[1], lP2[1]), cval(sP2[2], lP2[2]));
+  for (int k = 0; k < 6; ++k) tXX[k] = warp_sum(tXX[k]);
+  const bool linm = !(sp.flags & kNoLinMom), angm = !(sp.flags & kNoAngMom);
+  float3 cA2, dv, om;
+  momentum_step(sm, cA, M, iM, linm, angm, cA2, dv, om);
+  const float3 Pa = make_float3(sP2[0], sP2[1], sP2[2]);
   const float3 cA2d = iM * make_float3(tx2[0], tx2[1], tx2[2]);
   const float3 Pad = make_float3(tP2[0], tP2[1], tP2[2]);
   const float3 Lad = make_float3(tL2[0], tL2[1], tL2[2]) - cross(cA2d, Pa) - cross(cA2, Pad);
-  float3 dv = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
-  float3 dvd = dv, omd = om;
-  if (!(sp.flags & kNoLinMom)) {
-    dv = iM * momentum_dP(bm, sP2, lP2);
-    dvd = iM * (Pbd - Pad);
-  }
-  if (!(sp.flags & kNoAngMom)) {
-    const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
-                s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
-                s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
-    const float tr = s00 + s11 + s22;
-    solve_sym3(tr - s00, -s01, -s02, tr - s11, -s12, tr - s22, momentum_dL(bm, sL2, lL2, cA2, Pa), om);
+  float3 dvd = make_float3(0.f, 0.f, 0.f), omd = dvd;
+  if (linm) dvd = iM * (Pbd - Pad);
+  if (angm) {
+    float S[6];
+    body_second_moment(sm, cA2, M, S);
+    const float s00 = S[0], s01 = S[1], s02 = S[2], s11 = S[3], s12 = S[4], s22 = S[5];
+    const float tr = __fadd_rn(__fadd_rn(s00, s11), s22);
     // dS = dSXX - M (c' c^T + c c'^T) ; dI = tr(dS) I3 - dS
     const float d00 = tXX[0] - 2.f * M * cA2d.x * cA2.x;
     const float d01 = tXX[1] - M * (cA2d.x * cA2.y + cA2.x * cA2d.y);
@@ -803,7 +739,9 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
   const bool linm = !(sp.flags & kNoLinMom), angm = !(sp.flags & kNoAngMom);
 
   // ---- forward recomputation (as k_iterate) ----
-  float sx[3] = {0.f, 0.f, 0.f}, sA[9] = {0.f}, sP[3] = {0.f, 0.f, 0.f}, sL[3] = {0.f, 0.f, 0.f};
+  float s1[12], sP[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s1[k] = 0.f;
   for (int32_t p = p0 + lane; p < pe; p += 32) {
     const float4 xp = a.Xin[p], vp = a.Vin[p];
     const float3 dX = contact_dx(a, sp, p, xp, vp);
@@ -813,38 +751,17 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
     a.Vout[p] = make_float4(vb.x, vb.y, vb.z, 0.f);
     const float4 q = a.Q[p];
     const float m = q.w;
-    const float3 e = xb - anc;
-    const float3 me = m * e;
-    sx[0] += me.x; sx[1] += me.y; sx[2] += me.z;
-    sA[0] += me.x * q.x; sA[1] += me.x * q.y; sA[2] += me.x * q.z;
-    sA[3] += me.y * q.x; sA[4] += me.y * q.y; sA[5] += me.y * q.z;
-    sA[6] += me.z * q.x; sA[7] += me.z * q.y; sA[8] += me.z * q.z;
+    shape_terms(s1, m, xb - anc, q);
     sP[0] += m * vb.x; sP[1] += m * vb.y; sP[2] += m * vb.z;
-    const float3 l = cross(me, vb);
-    sL[0] += l.x; sL[1] += l.y; sL[2] += l.z;
-  }
-  float lx[3] = {0.f, 0.f, 0.f}, lP[3] = {0.f, 0.f, 0.f}, lL[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    warp_sum_c(sx[k], lx[k]);
-    warp_sum_c(sP[k], lP[k]);
-    warp_sum_c(sL[k], lL[k]);
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) sA[k] = warp_sum(sA[k]);
+  for (int k = 0; k < 12; ++k) s1[k] = warp_sum(s1[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sP[k] = warp_sum(sP[k]);
   const float iM = br.inv_mass, M = br.mass;
-  const float3 cA = iM * make_float3(cval(sx[0], lx[0]), cval(sx[1], lx[1]), cval(sx[2], lx[2]));
-  const BsmMoments bm = bsm_moments(sP, lP, sL, lL, cA);
-  const float3 Pb = bsm_P(bm);
   float A[9];
-  {
-    const float qs[3] = {br.qsx, br.qsy, br.qsz};
-    const float ca[3] = {cA.x, cA.y, cA.z};
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) A[3 * r + c] = sA[3 * r + c] - ca[r] * qs[c];
-  }
+  const float3 cA = shape_matrix(s1, iM, br.qsx, br.qsy, br.qsz, A);
+  const float3 Pb = make_float3(sP[0], sP[1], sP[2]);
   const float4 qrot = shape_rotation(A, a.quat[b]);
   float R[9];
   quat_to_mat(qrot, R);
@@ -852,7 +769,9 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
     return make_float3(R[0] * q.x + R[1] * q.y + R[2] * q.z, R[3] * q.x + R[4] * q.y + R[5] * q.z,
                        R[6] * q.x + R[7] * q.y + R[8] * q.z) + cA;
   };
-  float sx2[3] = {0.f, 0.f, 0.f}, sP2[3] = {0.f, 0.f, 0.f}, sL2[3] = {0.f, 0.f, 0.f}, sXX[6] = {0.f};
+  float sm[kMomentumSums];
+#pragma unroll
+  for (int k = 0; k < kMomentumSums; ++k) sm[k] = 0.f;
   for (int32_t p = p0 + lane; p < pe; p += 32) {
     const float4 xb4 = a.Xout[p], vb4 = a.Vout[p];
     const float4 q = a.Q[p];
@@ -861,32 +780,16 @@ __global__ void __launch_bounds__(128) k_iterate_adjoint_body(IterArgs a, Adjoin
     const float3 dsm = grel - (f3(xb4) - anc);
     const float3 xa = f3(xb4) + dsm;
     const float3 va = f3(vb4) + idt * dsm;
-    const float3 e = xa - anc;
-    const float3 me = m * e;
-    sx2[0] += me.x; sx2[1] += me.y; sx2[2] += me.z;
-    sP2[0] += m * va.x; sP2[1] += m * va.y; sP2[2] += m * va.z;
-    const float3 l = cross(me, va);
-    sL2[0] += l.x; sL2[1] += l.y; sL2[2] += l.z;
-    sXX[0] += me.x * e.x; sXX[1] += me.x * e.y; sXX[2] += me.x * e.z;
-    sXX[3] += me.y * e.y; sXX[4] += me.y * e.z; sXX[5] += me.z * e.z;
-  }
-  float lx2[3] = {0.f, 0.f, 0.f}, lP2[3] = {0.f, 0.f, 0.f}, lL2[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    warp_sum_c(sx2[k], lx2[k]);
-    warp_sum_c(sP2[k], lP2[k]);
-    warp_sum_c(sL2[k], lL2[k]);
+    momentum_terms(sm, m, f3(xb4) - anc - cA, f3(xb4), f3(vb4), xa, va, xa - anc);
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) sXX[k] = warp_sum(sXX[k]);
-  const float3 cA2 = iM * make_float3(cval(sx2[0], lx2[0]), cval(sx2[1], lx2[1]), cval(sx2[2], lx2[2]));
-  const float3 Pa = make_float3(cval(sP2[0], lP2[0]), cval(sP2[1], lP2[1]), cval(sP2[2], lP2[2]));
-  const float s00 = sXX[0] - M * cA2.x * cA2.x, s01 = sXX[1] - M * cA2.x * cA2.y,
-              s02 = sXX[2] - M * cA2.x * cA2.z, s11 = sXX[3] - M * cA2.y * cA2.y,
-              s12 = sXX[4] - M * cA2.y * cA2.z, s22 = sXX[5] - M * cA2.z * cA2.z;
-  const float trI = s00 + s11 + s22;
-  float3 om = make_float3(0.f, 0.f, 0.f);
-  if (angm) solve_sym3(trI - s00, -s01, -s02, trI - s11, -s12, trI - s22, momentum_dL(bm, sL2, lL2, cA2, Pa), om);
+  for (int k = 0; k < kMomentumSums; ++k) sm[k] = warp_sum(sm[k]);
+  float3 cA2, dv_unused, om;
+  momentum_step(sm, cA, M, iM, linm, angm, cA2, dv_unused, om);
+  float S[6];
+  body_second_moment(sm, cA2, M, S);
+  const float s00 = S[0], s01 = S[1], s02 = S[2], s11 = S[3], s12 = S[4], s22 = S[5];
+  const float trI = __fadd_rn(__fadd_rn(s00, s11), s22);
 
   // ---- backward: corrections -> dv~, w~ ----
   float sdv[3] = {0.f, 0.f, 0.f}, sw[3] = {0.f, 0.f, 0.f};

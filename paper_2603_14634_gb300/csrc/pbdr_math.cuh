@@ -186,46 +186,20 @@ __device__ __forceinline__ void solve_sym3(float s00, float s01, float s02, floa
 }
 
 // ---------------------------------------------------------------------------
-// Compensated body sums.  The momentum constraint (Sec. III-C, Eqs.
-// lin_momentum / ang_momentum) restores P and L from the difference of two
-// body sums taken a pass apart, so FP32 rounding of those sums is what FP32
-// leaves of the conservation.  The centroid, P and L sums are therefore carried
-// as unevaluated pairs s + lo: every addition of two partial sums is split by
-// Knuth's TwoSum into the rounded sum and its exact rounding error, which is
-// kept in lo.  The intrinsics fix the operations (no contraction), and TwoSum's
-// error term is unique, so both partners of a butterfly step get the same pair.
+// The momentum constraint (Sec. III-C, Eqs. lin_momentum / ang_momentum)
+// needs P_bsm - P_asm and L_asm - L_bsm.  With dx = x_asm - x_bsm and
+// dv = v_asm - v_bsm per particle (the differences of the stored FP32
+// values, exact in FP32 where the two lie within a factor of two of each
+// other) and dc = c_asm - c_bsm = sum m dx / M, exactly
+//   P_bsm - P_asm = -sum m dv,
+//   L_asm - L_bsm = sum m [ r_bsm x dv + dx x v_asm ] - dc x P_asm,
+// with r_bsm = x_bsm - c_bsm.  The terms are of the size of the
+// shape-matching correction, so these FP32 sums carry no cancellation,
+// unlike the difference of two whole-body sums, and they see the rounding
+// of the stored x_asm and v_asm.  The explicit intrinsics fix the rounding
+// of the per-particle terms, so every kernel that forms them gets the same
+// bits.
 // ---------------------------------------------------------------------------
-
-// a + b = s + e exactly (Knuth, The Art of Computer Programming vol. 2, 4.2.2)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (s, lo) <- (s, lo) + (s2, lo2)
-__device__ __forceinline__ void cadd(float &s, float &lo, float s2, float lo2) {
-  float e;
-  two_sum(s, s2, s, e);
-  lo = __fadd_rn(__fadd_rn(lo, lo2), e);
-}
-
-// butterfly warp sum of a compensated value; every lane ends with the same pair
-__device__ __forceinline__ void warp_sum_c(float &s, float &lo) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    cadd(s, lo, s2, l2);
-  }
-}
-
-__device__ __forceinline__ float cval(float s, float lo) { return __fadd_rn(s, lo); }
-
-// (a_s + a_l) - (b_s + b_l) with the two large parts subtracted first (exact
-// when they are within a factor of two, as two sums a pass apart are)
-__device__ __forceinline__ float cdiff(float as, float al, float bs, float bl) {
-  return __fadd_rn(__fsub_rn(as, bs), __fsub_rn(al, bl));
-}
 
 __device__ __forceinline__ float3 cross_rn(float3 a, float3 b) {
   return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
@@ -233,44 +207,98 @@ __device__ __forceinline__ float3 cross_rn(float3 a, float3 b) {
                      __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
 }
 
-// First-pass (X_bsm, V_bsm) quantities of a body kept for the momentum step:
-// P_bsm as a pair, the anchor-relative L sum's large part, and
-// lo(L sum) - (c_bsm - a) x P_bsm, so that L_bsm = Ls + T.
-struct BsmMoments {
-  float3 Ps, Pl, Ls, T;
-};
-
-__device__ __forceinline__ BsmMoments bsm_moments(const float *Ps, const float *Pl, const float *Ls,
-                                                  const float *Ll, float3 cA) {
-  BsmMoments r;
-  r.Ps = make_float3(Ps[0], Ps[1], Ps[2]);
-  r.Pl = make_float3(Pl[0], Pl[1], Pl[2]);
-  r.Ls = make_float3(Ls[0], Ls[1], Ls[2]);
-  const float3 P = make_float3(cval(Ps[0], Pl[0]), cval(Ps[1], Pl[1]), cval(Ps[2], Pl[2]));
-  const float3 cp = cross_rn(cA, P);
-  r.T = make_float3(__fsub_rn(Ll[0], cp.x), __fsub_rn(Ll[1], cp.y), __fsub_rn(Ll[2], cp.z));
-  return r;
+// Adds one particle's terms to the 12 first sums of shape matching:
+// s[0..2] sum m e, s[3..11] sum m e q^T (row major), e = x_bsm - anchor.
+__device__ __forceinline__ void shape_terms(float *s, float m, float3 e, float4 q) {
+  const float3 me = make_float3(__fmul_rn(m, e.x), __fmul_rn(m, e.y), __fmul_rn(m, e.z));
+  s[0] = __fadd_rn(s[0], me.x);
+  s[1] = __fadd_rn(s[1], me.y);
+  s[2] = __fadd_rn(s[2], me.z);
+  s[3] = __fmaf_rn(me.x, q.x, s[3]);
+  s[4] = __fmaf_rn(me.x, q.y, s[4]);
+  s[5] = __fmaf_rn(me.x, q.z, s[5]);
+  s[6] = __fmaf_rn(me.y, q.x, s[6]);
+  s[7] = __fmaf_rn(me.y, q.y, s[7]);
+  s[8] = __fmaf_rn(me.y, q.z, s[8]);
+  s[9] = __fmaf_rn(me.z, q.x, s[9]);
+  s[10] = __fmaf_rn(me.z, q.y, s[10]);
+  s[11] = __fmaf_rn(me.z, q.z, s[11]);
 }
 
-__device__ __forceinline__ float3 bsm_P(const BsmMoments &b) {
-  return make_float3(cval(b.Ps.x, b.Pl.x), cval(b.Ps.y, b.Pl.y), cval(b.Ps.z, b.Pl.z));
+// From the 12 first sums: c_bsm - anchor (cA) and A = sum m (x - c) q^T =
+// sum m (x - a) q^T - (c - a) (sum m q)^T
+__device__ __forceinline__ float3 shape_matrix(const float *s, float iM, float qsx, float qsy, float qsz,
+                                               float *A) {
+  const float3 cA = make_float3(__fmul_rn(iM, s[0]), __fmul_rn(iM, s[1]), __fmul_rn(iM, s[2]));
+  const float ca[3] = {cA.x, cA.y, cA.z}, qs[3] = {qsx, qsy, qsz};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = __fsub_rn(s[3 + 3 * r + c], __fmul_rn(ca[r], qs[c]));
+  return cA;
 }
 
-// P_bsm - P_asm from the pairs
-__device__ __forceinline__ float3 momentum_dP(const BsmMoments &b, const float *Pas, const float *Pal) {
-  return make_float3(cdiff(b.Ps.x, b.Pl.x, Pas[0], Pal[0]), cdiff(b.Ps.y, b.Pl.y, Pas[1], Pal[1]),
-                     cdiff(b.Ps.z, b.Pl.z, Pas[2], Pal[2]));
+// Adds one particle's terms to the kMomentumSums sums of the momentum step:
+// s[0..2] sum m dv, s[3..5] sum m dx, s[6..8] sum m (r_bsm x dv + dx x v_asm),
+// s[9..11] sum m v_asm, s[12..17] sum m e e^T (upper triangle,
+// e = x_asm - anchor) for the inertia.
+constexpr int kMomentumSums = 18;
+__device__ __forceinline__ void momentum_terms(float *s, float m, float3 rb, float3 xb, float3 vb, float3 xa,
+                                               float3 va, float3 e) {
+  const float3 dx = make_float3(__fsub_rn(xa.x, xb.x), __fsub_rn(xa.y, xb.y), __fsub_rn(xa.z, xb.z));
+  const float3 dv = make_float3(__fsub_rn(va.x, vb.x), __fsub_rn(va.y, vb.y), __fsub_rn(va.z, vb.z));
+  s[0] = __fmaf_rn(m, dv.x, s[0]);
+  s[1] = __fmaf_rn(m, dv.y, s[1]);
+  s[2] = __fmaf_rn(m, dv.z, s[2]);
+  s[3] = __fmaf_rn(m, dx.x, s[3]);
+  s[4] = __fmaf_rn(m, dx.y, s[4]);
+  s[5] = __fmaf_rn(m, dx.z, s[5]);
+  const float3 a = cross_rn(rb, dv), b = cross_rn(dx, va);
+  s[6] = __fmaf_rn(m, __fadd_rn(a.x, b.x), s[6]);
+  s[7] = __fmaf_rn(m, __fadd_rn(a.y, b.y), s[7]);
+  s[8] = __fmaf_rn(m, __fadd_rn(a.z, b.z), s[8]);
+  s[9] = __fmaf_rn(m, va.x, s[9]);
+  s[10] = __fmaf_rn(m, va.y, s[10]);
+  s[11] = __fmaf_rn(m, va.z, s[11]);
+  const float3 me = make_float3(__fmul_rn(m, e.x), __fmul_rn(m, e.y), __fmul_rn(m, e.z));
+  s[12] = __fmaf_rn(me.x, e.x, s[12]);
+  s[13] = __fmaf_rn(me.x, e.y, s[13]);
+  s[14] = __fmaf_rn(me.x, e.z, s[14]);
+  s[15] = __fmaf_rn(me.y, e.y, s[15]);
+  s[16] = __fmaf_rn(me.y, e.z, s[16]);
+  s[17] = __fmaf_rn(me.z, e.z, s[17]);
 }
 
-// L_asm - L_bsm, both about their own centre of mass: L = (anchor-relative
-// sum) - (c - a) x P; the large parts of the two sums are subtracted first
-__device__ __forceinline__ float3 momentum_dL(const BsmMoments &b, const float *Las, const float *Lal,
-                                              float3 cA2, float3 Pa) {
-  const float3 cp = cross_rn(cA2, Pa);
-  const float3 Ta = make_float3(__fsub_rn(Lal[0], cp.x), __fsub_rn(Lal[1], cp.y), __fsub_rn(Lal[2], cp.z));
-  return make_float3(__fadd_rn(__fsub_rn(Las[0], b.Ls.x), __fsub_rn(Ta.x, b.T.x)),
-                     __fadd_rn(__fsub_rn(Las[1], b.Ls.y), __fsub_rn(Ta.y, b.T.y)),
-                     __fadd_rn(__fsub_rn(Las[2], b.Ls.z), __fsub_rn(Ta.z, b.T.z)));
+// S = sum m r r^T about c_asm from the anchor-relative sums s[12..17]
+// (upper triangle: s00 s01 s02 s11 s12 s22)
+__device__ __forceinline__ void body_second_moment(const float *s, float3 cA2, float M, float *S) {
+  const float3 Mc = make_float3(__fmul_rn(M, cA2.x), __fmul_rn(M, cA2.y), __fmul_rn(M, cA2.z));
+  S[0] = __fsub_rn(s[12], __fmul_rn(Mc.x, cA2.x));
+  S[1] = __fsub_rn(s[13], __fmul_rn(Mc.x, cA2.y));
+  S[2] = __fsub_rn(s[14], __fmul_rn(Mc.x, cA2.z));
+  S[3] = __fsub_rn(s[15], __fmul_rn(Mc.y, cA2.y));
+  S[4] = __fsub_rn(s[16], __fmul_rn(Mc.y, cA2.z));
+  S[5] = __fsub_rn(s[17], __fmul_rn(Mc.z, cA2.z));
+}
+
+// From the body totals of momentum_terms: c_asm - anchor (cA2),
+// dv = (P_bsm - P_asm) / M and w = I^-1 (L_asm - L_bsm) with I about c_asm
+// (either left 0 when its part of the constraint is switched off).
+__device__ __forceinline__ void momentum_step(const float *s, float3 cA, float M, float iM, bool lin, bool ang,
+                                              float3 &cA2, float3 &dv, float3 &om) {
+  const float3 dc = make_float3(__fmul_rn(iM, s[3]), __fmul_rn(iM, s[4]), __fmul_rn(iM, s[5]));
+  cA2 = make_float3(__fadd_rn(cA.x, dc.x), __fadd_rn(cA.y, dc.y), __fadd_rn(cA.z, dc.z));
+  dv = lin ? make_float3(-__fmul_rn(iM, s[0]), -__fmul_rn(iM, s[1]), -__fmul_rn(iM, s[2])) : make_float3(0.f, 0.f, 0.f);
+  om = make_float3(0.f, 0.f, 0.f);
+  if (ang) {
+    const float3 cp = cross_rn(dc, make_float3(s[9], s[10], s[11]));
+    const float3 dL = make_float3(__fsub_rn(s[6], cp.x), __fsub_rn(s[7], cp.y), __fsub_rn(s[8], cp.z));
+    float S[6];
+    body_second_moment(s, cA2, M, S);
+    const float tr = __fadd_rn(__fadd_rn(S[0], S[3]), S[5]);
+    // I = tr(S) I3 - S
+    solve_sym3(tr - S[0], -S[1], -S[2], tr - S[3], -S[4], tr - S[5], dL, om);
+  }
 }
 
 }  // namespace

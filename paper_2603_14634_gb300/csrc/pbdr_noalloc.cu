@@ -108,8 +108,9 @@ __global__ void k_na_neighbors(const float *__restrict__ pos, const int32_t *__r
           const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
           if (!(d2 < Rn2)) continue;
           const int32_t q = (int32_t)svals[j];
-          if (cnt < cap) {
-            int at = cnt;
+          // keep the cap lowest indices, ascending: a full list drops its largest
+          if (cnt < cap || q < list[cap - 1]) {
+            int at = cnt < cap ? cnt : cap - 1;
             while (at > 0 && list[at - 1] > q) {
               list[at] = list[at - 1];
               --at;

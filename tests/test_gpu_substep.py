@@ -2,80 +2,35 @@
 
 Tolerances (one substep):
 - positions within 1e-5 m;
-- per-body linear momentum within 1e-6 of the body's momentum scale
-  sum_p m_p |v_p|; angular momentum within 4 K 2^-24 of sum_p m_p |r_p| |v_p|
-  (every one of the K iterations re-rounds r, v and the body sums in FP32,
-  which bounds how well L can be carried: 2.4e-6 at K = 10, 4.8e-6 at
-  K = 20); plus, for bodies that
-  touch the ground or another body, the FP32 resolution of the contact
-  impulses: each of the K iterations computes a contact correction from FP32
-  positions, good to a few units in the last place u(|x|) of the coordinates,
-  i.e. (K/dt) sum_{p in contact} m_p 8 u(|x_p|) in momentum (times the body
-  radius for L).  A resting body's bottom layer sits ~1e-5 m deep with
-  u(0.05 m) = 3.7e-9 m, so its support impulse is only resolved to ~4e-4.
+- per-body momentum (tests/momentum_bounds.py): free bodies within 1e-6 of
+  sum m|v| (P) and of sum m|r||v| (L); bodies in contact within that plus a
+  multiple of the oracle's own response, on the same state, to a one-ulp
+  change of the FP32 predicted positions.
 Trajectories: errors against the closed forms of the analytic tests within
 1.05x the oracle's own error + 1e-4.
 """
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
 
 from paper_2603_14634_gb300 import scenes
 
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+from momentum_bounds import check_momenta  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 POS_TOL = 1e-5
-MOM_TOL = 1e-6
 G = 9.81
 
 
-def _ulp32(x):
-    x = np.maximum(np.abs(x), 1e-30)
-    return 2.0 ** (np.floor(np.log2(x)) - 23)
-
-
-def _contact_particles(orc, sc, *states):
-    """particles within the contact band (2.2 r of another body, 1.5 r of the
-    ground) in any of the given FP32/FP64 states"""
-    bid = orc.body_index(sc.body_off)
-    n = np.array(sc.plane[:3], np.float64)
-    hit = np.zeros(sc.num_particles, bool)
-    for x in states:
-        off, idx = orc.neighbors(np.asarray(x, np.float32), bid, sc.radius)
-        hit |= np.diff(off) > 0
-        hit |= (np.asarray(x, np.float64) @ n - sc.plane[3]) < 1.5 * sc.radius
-    return hit
-
-
-def _check_momenta(orc, sc, x0, pos, vel, o, label, check_P=True, check_L=True):
-    m = 1.0 / sc.inv_mass.astype(np.float64)
-    hit = _contact_particles(orc, sc, x0, pos, o.x)
-    K, dt = sc.iterations, sc.dt
-    worst = 0.0
-    for b in range(sc.num_bodies):
-        s0, s1 = sc.body_off[b], sc.body_off[b + 1]
-        mb = m[s0:s1, None]
-        vg, vo = vel[s0:s1].astype(np.float64), o.v[s0:s1]
-        cg = (mb * pos[s0:s1]).sum(0) / mb.sum()
-        co = (mb * o.x[s0:s1]).sum(0) / mb.sum()
-        rg, ro = pos[s0:s1] - cg, o.x[s0:s1] - co
-        dP = np.linalg.norm((mb * vg).sum(0) - (mb * vo).sum(0))
-        dL = np.linalg.norm(np.cross(rg, mb * vg).sum(0) - np.cross(ro, mb * vo).sum(0))
-        sP = (mb[:, 0] * np.linalg.norm(vo, axis=1)).sum()
-        sL = (mb[:, 0] * np.linalg.norm(ro, axis=1) * np.linalg.norm(vo, axis=1)).sum()
-        xmag = np.maximum(np.abs(o.x[s0:s1]).max(1), sc.radius)
-        contact = (K / dt) * (mb[:, 0] * 8 * _ulp32(xmag))[hit[s0:s1]].sum()
-        rad = np.linalg.norm(ro, axis=1).max() + sc.radius
-        boundP = MOM_TOL * sP + contact
-        boundL = 4 * K * 2.0 ** -24 * sL + contact * rad
-        if check_P:
-            assert dP <= boundP, f"{label}: body {b} |dP| {dP:.3e} > {boundP:.3e} (contact part {contact:.2e})"
-        if check_L:
-            assert dL <= boundL, f"{label}: body {b} |dL| {dL:.3e} > {boundL:.3e}"
-        if not hit[s0:s1].any():
-            worst = max(worst, dP / max(sP, 1e-30))
-    return worst
+def _check_momenta(orc, sc, x0, pos, vel, o, label, state32, check_P=True, check_L=True):
+    """x0: the oracle's start state (FP64); state32: the FP32 (x, v) both
+    sides started from."""
+    return check_momenta(orc, sc, x0, pos, vel, o, label, state32, check_P, check_L)
 
 
 def _compare_one_substep(ctx, orc, sc, state=None, label="", check_P=True, check_L=True):
@@ -86,6 +41,8 @@ def _compare_one_substep(ctx, orc, sc, state=None, label="", check_P=True, check
         pos32, vel32 = (np.ascontiguousarray(a, np.float32) for a in state)
         ctx.write_state(sid, pos32, vel32)
         o.set_state(pos32, vel32)
+    else:
+        pos32, vel32 = (np.ascontiguousarray(a, np.float32) for a in (sc.pos, sc.vel))
     x_start = o.x.copy()
     ctx.step(sid, 1)
     pos, vel, err = ctx.read_state(sid)
@@ -93,7 +50,7 @@ def _compare_one_substep(ctx, orc, sc, state=None, label="", check_P=True, check
     assert err == 0, f"{label}: error bits {err}"
     dx = np.abs(pos - o.x).max()
     assert dx <= POS_TOL, f"{label}: max |dx| {dx}"
-    rel = _check_momenta(orc, sc, x_start, pos, vel, o, label, check_P, check_L)
+    rel = _check_momenta(orc, sc, x_start, pos, vel, o, label, (pos32, vel32), check_P, check_L)
     return dx, rel
 
 
@@ -145,7 +102,7 @@ def test_batched_scenes_one_substep(ctx, orc):
         pos, vel, err = ctx.read_state(sid)
         assert err == 0
         assert np.abs(pos - o.x).max() <= POS_TOL
-        _check_momenta(orc, sc, x, pos, vel, o, f"batched scene {sid}")
+        _check_momenta(orc, sc, x, pos, vel, o, f"batched scene {sid}", (x, v))
 
 
 def test_wrench_one_substep(ctx, orc):
@@ -316,7 +273,7 @@ def test_mixed_sizes_every_class_and_streaming_rest(ctx, orc):
         pos, vel, err = ctx.read_state(sid)
         assert err == 0
         assert np.abs(pos - o.x).max() <= POS_TOL, f"scene of {sc.num_particles}"
-        _check_momenta(orc, sc, x, pos, vel, o, f"scene of {sc.num_particles}")
+        _check_momenta(orc, sc, x, pos, vel, o, f"scene of {sc.num_particles}", (x, v))
 
 
 def test_nonfinite_state_is_reported(ctx, pbdr_lib):
