@@ -141,3 +141,29 @@ def test_results_identical_alone_and_in_the_mix(pbdr_lib):
         gpos, gvel, gerr = srv.results[rid]
         assert err == gerr == 0
         assert np.array_equal(pos, gpos) and np.array_equal(vel, gvel)
+
+
+@pytest.mark.gpu
+def test_served_results_match_oracle(pbdr_lib, orc):
+    """Every request served by continuous batching (staggered arrivals,
+    requests of 10^3 to 10^4 particles, so that both the scene-resident
+    kernel and the streaming form run in the same ticks) ends within the
+    position tolerance of the oracle stepping the same scene alone."""
+    rng = np.random.default_rng(12)
+    reqs = []
+    for k in range(6):
+        sc, _ = scenes.serving_request(rng, min_particles=1000, max_particles=12000)
+        reqs.append((sc, int(rng.integers(2, 8)), 0.003 * k))
+    assert max(sc.num_particles for sc, _, _ in reqs) > 8192   # one takes the streaming form
+    srv = Server(hbm_budget_bytes=4 << 30)
+    ids = [srv.submit(sc, steps, arrival=t) for sc, steps, t in reqs]
+    st = srv.run(realtime=True)
+    assert st["requests"] == len(reqs)
+    assert len(srv.tick_ms) == st["ticks"] and min(srv.tick_ms) > 0
+    for rid, (sc, steps, _) in zip(ids, reqs):
+        gpos, gvel, gerr = srv.results[rid]
+        assert gerr == 0
+        o = orc.OracleScene(sc)
+        o.substep(steps)
+        dx = np.abs(gpos - o.x).max()
+        assert dx <= 1e-5, f"request {rid} ({sc.num_particles} particles, {steps} substeps): |dx| {dx:.2e}"
