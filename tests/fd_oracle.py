@@ -52,3 +52,40 @@ def mu_fd(orc, scene, steps, h=1e-4):
         sc.friction = float(scene.friction) + sgn * h
         out.append(final_coms(orc, sc, steps).reshape(-1))
     return (out[0] - out[1]) / (2 * h)
+
+
+def _fd_column(args):
+    """One central-difference column (runs in a spawned worker)."""
+    from oracle import oracle as orc
+    scene_dict, v_lin, w_ang, b, k, steps, h = args
+    scene = scenes.Scene(**scene_dict)
+    out = []
+    for sgn in (1.0, -1.0):
+        if b < 0:   # the friction coefficient
+            sc = scenes.Scene(**scene_dict)
+            sc.friction = float(scene.friction) + sgn * h
+        else:
+            v = np.array(v_lin, np.float64).copy()
+            w = np.array(w_ang, np.float64).copy()
+            (v if k < 3 else w)[b, k % 3] += sgn * h
+            sc = scenes.Scene(**scene_dict)
+            sc.vel = diff.rigid_velocity(scene, v, w)
+        out.append(final_coms(orc, sc, steps).reshape(-1))
+    return (out[0] - out[1]) / (2 * h)
+
+
+def rigid_mu_fd_jacobian_parallel(scene, v_lin, w_ang, steps, h=1e-4, workers=None):
+    """d(final CoM [3B]) / d(v, omega [6B], mu) [3B, 6B + 1] by central
+    differences of the FP64 oracle, one column per task on a pool of
+    spawned processes (never forked: the caller may hold a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    B = scene.num_bodies
+    d = dict(scene.__dict__)
+    tasks = [(d, v_lin, w_ang, b, k, steps, h) for b in range(B) for k in range(6)]
+    tasks.append((d, v_lin, w_ang, -1, 0, steps, h))
+    workers = workers or min(16, os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        cols = list(ex.map(_fd_column, tasks))
+    return np.stack(cols, 1)
