@@ -58,7 +58,8 @@ def parse_args():
     ap.add_argument("--ref-sample-scenes", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the Poisson arrival trace of the serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=300.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0,
+                    help="Poisson arrival rate of the serving run (the serving workload's 2000/s)")
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
     ap.add_argument("--path", choices=["resident", "streaming"], default="resident",
@@ -68,6 +69,13 @@ def parse_args():
                     help="default launch shapes instead of tuned ones")
     ap.add_argument("--grad-steps", type=int, default=200,
                     help="substeps of the differentiated 16-body run (0: skip)")
+    ap.add_argument("--dense-scenes", type=int, default=152,
+                    help="scenes of the contact-dense secondary line (0: skip)")
+    ap.add_argument("--dense-steps", type=int, default=50)
+    ap.add_argument("--strong", action="store_true",
+                    help="under torchrun: split ONE batch (the seed's) over the ranks by "
+                         "longest-processing-time on particle counts (strong scaling) instead of "
+                         "giving every rank its own batch (weak scaling)")
     ap.add_argument("--settle", type=int, default=240,
                     help="substeps run before the warm-up so that bodies have landed and touch")
     a = ap.parse_args()
@@ -269,7 +277,14 @@ def run_pbdr(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    scs = make_workload(args, args.seed + rank)     # weak scaling: own batch per rank
+    if args.strong:   # strong scaling: this rank's LPT share of one batch
+        from paper_2603_14634_gb300.shard import lpt_partition
+        scs_job = make_workload(args, args.seed)
+        mine = lpt_partition([s.num_particles for s in scs_job], world)[rank]
+        scs = [scs_job[i] for i in mine]
+    else:             # weak scaling: own batch per rank
+        scs = make_workload(args, args.seed + rank)
+        scs_job = scs
     ctx = Context(local_rank)
     if args.no_autotune:
         from paper_2603_14634_gb300.binding import OPT_AUTOTUNE
@@ -415,6 +430,11 @@ def run_pbdr(args, rank, world, local_rank):
         bs_ms = a.elapsed_time(b)
     batched_sample_value = s_work * args.per_scene_steps / (bs_ms * 1e-3)
 
+    shards = None
+    if dist is not None:
+        from paper_2603_14634_gb300.shard import gather_to_rank0
+        shards = gather_to_rank0({"rank": rank, "scenes": len(ids), "particles": n_particles,
+                                  "timed_ms": round(ms_total, 3)}, dist)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -473,9 +493,11 @@ def run_pbdr(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": workload_config(scs, args),
+        "higher_is_better": True, "scaling": "strong" if args.strong else "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(scs_job, args, {"parallelism": (
+            "one batch split over the ranks (LPT by particle count), one GPU per rank"
+            if args.strong else "scene batch per GPU")} if world > 1 else None),
         "p50_step_ms": round(lat[len(lat) // 2], 4),
         "p99_step_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
         "per_scene_launch": {
@@ -494,6 +516,8 @@ def run_pbdr(args, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
     }
+    if shards is not None:
+        line["shards"] = shards
     if issue is not None:
         line["roofline_issue"] = issue
     if dom == "scene_resident":
@@ -513,6 +537,8 @@ def run_pbdr(args, rank, world, local_rank):
         "frac": round(b_model * value / world / 1e9 / peak, 4),
         "what": "per-GPU throughput x bytes a state-streaming substep would move (not DRAM traffic)",
     }
+    if world == 1 and args.dense_scenes > 0 and args.dense_steps > 0:
+        line["contact_dense"] = run_contact_dense(args, local_rank, peak)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args, local_rank)
     if world == 1 and args.grad_steps > 0:
@@ -529,6 +555,52 @@ def run_pbdr(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+def run_contact_dense(args, local_rank, peak):
+    """Secondary line with particle-particle contact everywhere: a batch of
+    stacked blocks (125 bodies of 4^3 each, 8000 particles, faces one
+    particle diameter apart, K = 20), timed after settling, so that the
+    contact gather is inside a timed number."""
+    import torch
+    from paper_2603_14634_gb300 import scenes
+    from paper_2603_14634_gb300.binding import Context
+    scs = scenes.stacked_block_scenes(args.dense_scenes, seed=args.seed + 5000,
+                                      workers=max(1, min(os.cpu_count() or 1, 32)))
+    n = sum(s.num_particles for s in scs)
+    work = sum(s.num_particles * s.iterations for s in scs)
+    K = scs[0].iterations
+    out = {"what": "stacked blocks of 125 bodies of 4^3 (8000 particles each) resting on the "
+                   "ground with touching faces, K = 20, one batched pbdr_step per substep",
+           "scenes": len(scs), "particles": n, "iterations": K, "settle_substeps": 24}
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    with Context(local_rank) as ctx, torch.cuda.stream(stream):
+        ids = [ctx.create_scene(s) for s in scs]
+        for path in ("resident", "streaming"):
+            ctx.set_path(streaming=path == "streaming")
+            ctx.step(ids, 24 if path == "resident" else 2, sh)
+            stream.synchronize()
+            kbar = ctx.neighbor_total(ids, sh) / n
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.dense_steps):
+                ctx.step(ids, 1, sh)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / args.dense_steps
+            _, _, err = ctx.read_states(ids, stream=sh)
+            value = work / (ms * 1e-3)
+            b_model = 100.0 + 4.0 * kbar + (184.0 + 4.0 * kbar) / K
+            rec = {"value": round(value, 1), "unit": UNIT, "ms_per_step": round(ms, 4),
+                   "kbar": round(kbar, 3), "scenes_with_error_bits": int((err != 0).sum()),
+                   "streaming_model_frac": round(b_model * value / 1e9 / peak, 4),
+                   "compulsory_frac": round((84.0 + 4.0 * kbar) * n / (ms * 1e-3) / 1e9 / peak, 4)}
+            out[path] = rec
+    out["note"] = ("streaming_model_frac prices the throughput at 100 + 4 kbar + (184 + 4 kbar)/K B "
+                   "per particle-iteration, compulsory_frac at 84 + 4 kbar B per particle-substep, "
+                   "both against the measured HBM copy bandwidth")
+    return out
 
 
 def run_gradient(args, local_rank):

@@ -271,6 +271,53 @@ def batched_scenes(num_scenes: int = 4096, seed: int = 0, workers: int = 0,
     return [_batch_scene_from_seed(j) for j in jobs]
 
 
+def stacked_block_scene(seed: int = 0, nb: int = 5, n: int = 4, pitch: float = 0.4,
+                        tilt_deg: float = 0.5, shift: float = 0.002, friction: float = 0.5,
+                        dt: float = 1.0 / 240.0, iterations: int = 20) -> Scene:
+    """A contact-dense scene: nb^3 rigid n^3 bodies (spacing 0.1 m, r = 0.05 m)
+    stacked in a block on the ground, at rest, with a pitch that puts the
+    facing particles of neighbouring bodies one diameter apart; every body is
+    tilted by up to ``tilt_deg`` about a random axis and shifted by up to
+    ``shift`` m, so the faces are not exactly aligned.  Defaults: 125 bodies
+    of 4^3 (8000 particles, the size of the 64-body scene), 20 iterations;
+    after a tenth of a second the particles average about one neighbour."""
+    rng = np.random.default_rng(seed)
+    spacing = 0.1
+    base = lattice_cube(n, spacing)
+    base = base - base.mean(0)
+    half = 0.5 * (n - 1) * spacing
+    pos, vel = [], []
+    for iz in range(nb):
+        for iy in range(nb):
+            for ix in range(nb):
+                axis = rng.normal(size=3)
+                axis /= np.linalg.norm(axis)
+                ang = math.radians(tilt_deg) * rng.uniform(-1.0, 1.0)
+                K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+                R = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)
+                c = np.array([ix * pitch, iy * pitch, 0.05 + half + iz * pitch + 0.002 * iz])
+                c[:2] -= 0.5 * (nb - 1) * pitch
+                c = c + rng.uniform(-shift, shift, size=3) * np.array([1.0, 1.0, 0.0])
+                pos.append(base @ R.T + c)
+                vel.append(np.zeros_like(base))
+    return _assemble(pos, vel, 1.0, friction=friction, dt=dt, iterations=iterations)
+
+
+def _stacked_from_seed(args):
+    seed, kw = args
+    return stacked_block_scene(seed=seed, **kw)
+
+
+def stacked_block_scenes(num_scenes: int, seed: int = 0, workers: int = 0, **kw) -> List[Scene]:
+    """``num_scenes`` stacked blocks (seeds seed, seed+1, ...)."""
+    jobs = [(seed + k, kw) for k in range(num_scenes)]
+    if workers and workers > 1 and num_scenes > 16:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            return pool.map(_stacked_from_seed, jobs, chunksize=4)
+    return [_stacked_from_seed(j) for j in jobs]
+
+
 def resting_grid_scene(seed: int = 0, nx: int = 4, n: int = 5, pitch: float = 0.6,
                        friction: float = 0.5, dt: float = 1.0 / 240.0,
                        iterations: int = 10, radius: float = 0.05,

@@ -51,7 +51,11 @@ def _rank_main(rank, world, port, out_dir):
         out[i] = o.x.copy()
     t = max_over_ranks(float(rank + 1), dist)
     got = gather_to_rank0(out, dist)
+    stepped = gather_to_rank0(list(mine), dist)
     if rank == 0:
+        # every scene of the batch is stepped by exactly one rank
+        flat = [i for part in stepped for i in part]
+        assert sorted(flat) == list(range(len(scs))), flat
         merged = {}
         for part in got:
             merged.update(part)
