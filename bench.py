@@ -239,11 +239,12 @@ def ncu_traffic(kernel):
 
 # FP32 operations of the method per particle, counted from the arithmetic of
 # the scene-resident kernel (an FMA counts 2): per solver iteration the
-# contact pass without contacts (ground test, X_bsm, V_bsm, 18 first sums) 61,
-# the goal pass (goals, X_asm, V_asm, 15 second sums) 81, the momentum
-# correction 27; per substep the integration 12.  Contacts, the per-body
-# rotation and momentum solves and the neighbour build are not counted.
-FLOPS_PER_PARTICLE_ITERATION = 61 + 81 + 27
+# contact pass without contacts (ground test, X_bsm, the 12 shape-matching
+# sums) 37, the goal pass (V_bsm, goals, X_asm, V_asm, the 18 sums of the
+# momentum step) 117, the momentum correction 27; per substep the
+# integration 12.  Contacts, the per-body rotation and momentum solves and
+# the neighbour build are not counted.
+FLOPS_PER_PARTICLE_ITERATION = 37 + 117 + 27
 FLOPS_PER_PARTICLE_SUBSTEP = 12
 FP32_LANES_PER_SM = 128
 

@@ -11,9 +11,9 @@ import bench  # noqa: E402
 def test_alu_roofline_arithmetic():
     r = bench.alu_roofline(10.0, 5_033_654, 1.94e-3, 152, 2070.0)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["flops_per_unit"] == 169 * 10 + 12
+    assert r["flops_per_unit"] == 181 * 10 + 12
     assert abs(r["peak"] - 152 * 128 * 2 * 2.07e9 / 1e12) < 0.01          # 80.55 TFLOP/s
-    assert abs(r["achieved"] - 1702 * 5_033_654 / 1.94e-3 / 1e12) < 1e-3
+    assert abs(r["achieved"] - 1822 * 5_033_654 / 1.94e-3 / 1e12) < 1e-3
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
 
 
