@@ -277,7 +277,8 @@ int pbdr_read_adjoint_friction(pbdr_ctx *ctx, pbdr_scene scene, double *mubar, v
 /* Launch shapes of the scene-resident kernel for the scene set ids[0..n):
  * out[5k..5k+4] = {particle capacity, scenes, threads per CTA, scratch bits
  * (1: velocities in shared memory, 2: per-particle scratch in shared memory),
- * CTAs} for size class k = 0..3 (cap >= 20). */
+ * CTAs} for size class k = 0..3 (capacities 1024, 2048, 4096 and 8192
+ * particles; cap >= 20). */
 int pbdr_plan_config(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, int32_t *out, int32_t cap);
 
 /* Launch statistics of the last pbdr_step call: the number of kernel

@@ -301,13 +301,16 @@ def pbdr_set_option(ctx: int, option: int, value: int) -> None:
     _check(load().pbdr_set_option(ctx, option, value))
 
 
+NUM_CLASSES = 4   # size classes of the scene-resident kernel
+
+
 def pbdr_plan_config(ctx: int, ids: Sequence[int]):
-    """-> list of per-class dicts (capacity, scenes, threads, v_shared, ctas)"""
+    """-> list of per-class dicts (capacity, scenes, threads, scratch bits, ctas)"""
     arr, p = _ids(ids)
-    out = np.zeros(20, np.int32)
-    _check(load().pbdr_plan_config(ctx, p, len(arr), _ptr(out), 20))
+    out = np.zeros(5 * NUM_CLASSES, np.int32)
+    _check(load().pbdr_plan_config(ctx, p, len(arr), _ptr(out), out.size))
     keys = ("capacity", "scenes", "threads", "scratch_bits", "ctas")
-    return [dict(zip(keys, map(int, out[5 * k:5 * k + 5]))) for k in range(4)]
+    return [dict(zip(keys, map(int, out[5 * k:5 * k + 5]))) for k in range(NUM_CLASSES)]
 
 
 def pbdr_read_neighbors(ctx: int, scene: int, stream=None, lists_only: bool = False):

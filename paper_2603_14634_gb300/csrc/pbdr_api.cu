@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pbdr_internal.cuh"
@@ -35,6 +36,31 @@ int fail(int code, const std::string &msg) {
   } while (0)
 
 // owned device allocation
+// page-locked host memory (grow-only staging for uploads)
+struct PinnedBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf &) = delete;
+  PinnedBuf &operator=(const PinnedBuf &) = delete;
+  ~PinnedBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  cudaError_t grow(size_t n) {
+    if (bytes >= n) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    const cudaError_t e = cudaHostAlloc(&p, n, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+  }
+};
+
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
@@ -106,6 +132,9 @@ struct SceneHost {
 // segment tables, wrench and class lists) live in `tab` and are copied into
 // the context's table buffer, in stream order, when the plan becomes the
 // active one; the streaming form's sort and cell scratch is the context's.
+// size classes of the scene-resident kernel (particle capacities below)
+constexpr int kNumClasses = 4;
+
 struct Plan {
   std::vector<int32_t> ids;
   int32_t np = 0, nb = 0;
@@ -135,7 +164,7 @@ struct Plan {
     std::vector<int32_t> ids;
     int32_t o_list = -1;           // offset of the scene list in tab
   };
-  std::array<FClass, 4> classes;
+  std::array<FClass, kNumClasses> classes;
   std::unique_ptr<Plan> rest;      // scenes too large for a class (streaming form)
   bool tuned = false;              // launch shapes picked by the autotuner
   cudaGraphExec_t graph = nullptr; // one substep, captured
@@ -154,8 +183,8 @@ struct Plan {
 constexpr size_t kMaxCachedPlans = 1024;
 constexpr int64_t kTuneAfter = 128;   // substeps of a plan before its launch shapes are tuned
 
-constexpr int kClassCaps[4] = {1024, 2048, 4096, 8192};
-constexpr int kClassThreads[4] = {256, 256, 512, 512};
+constexpr int kClassCaps[kNumClasses] = {1024, 2048, 4096, 8192};
+constexpr int kClassThreads[kNumClasses] = {256, 256, 512, 512};
 // dynamic shared memory a class layout may use: the 227 KB a CTA may opt in
 // to, less 1 KB for the kernel's static shared variables
 constexpr size_t kFusedSmemLimit = 226 * 1024;
@@ -192,8 +221,8 @@ struct pbdr_ctx {
   DevBuf bodies, wrench, quat, bcom, biter, border;
   DevBuf dx_scratch, tickets, chunks, partials;
   int32_t ccap = 0, nc_used = 0;   // chunk (and partial-slot) capacity / use
-  cudaStream_t cls_stream[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t cls_stream[kNumClasses] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kNumClasses] = {};
   int path = 0;                    // 0: scene-resident where a scene fits, 1: streaming only
   bool use_graphs = true;          // replay a captured CUDA graph per substep
   bool autotune = true;            // time launch shapes on the first step of a plan
@@ -210,11 +239,14 @@ struct pbdr_ctx {
   std::map<std::pair<int, int32_t>, std::array<int, 4>> tune_memo;
   // tables of the active plan and the streaming form's scratch (grow-only)
   DevBuf tab, s_keys_a, s_keys_b, s_vals_a, s_vals_b, s_hist, s_cells, s_spos, s_pmap, s_bmap;
+  DevBuf s_bounds, s_near;         // streaming neighbour culling: body boxes, near bodies
   const Plan *active = nullptr;
   uint64_t gen = 1;                // bumped whenever a device buffer moves (graphs recapture)
   Plan *last_nbr_plan = nullptr;
   int64_t last_launches = 0;
   DevBuf stage_pos, stage_vel, seg_p0, seg_off, err_ids, err_out;
+  // scene uploads: pinned staging
+  PinnedBuf up_stage;
   // stage profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -322,6 +354,9 @@ int dev_grow(pbdr_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
   if (e != cudaSuccess) return fail(PBDR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   if (b.p && keep) {
     e = cudaMemcpy(np, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice);
+    // a device-to-device copy may still run when cudaMemcpy returns: finish
+    // it before anything else writes the new buffer on another stream
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       cudaFree(np);
       return fail(PBDR_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
@@ -492,15 +527,15 @@ int fill_fused_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P) {
   for (int32_t i = 0; i < n; ++i) {
     const SceneHost &S = c->sh[ids[i]];
     int k = 0;
-    while (k < 4 && S.np > kClassCaps[k]) ++k;
-    if (k < 4)
+    while (k < kNumClasses && S.np > kClassCaps[k]) ++k;
+    if (k < kNumClasses)
       P.classes[k].ids.push_back(ids[i]);
     else
       rest.push_back(ids[i]);
   }
   if (!c->num_sms) CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   int rc;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNumClasses; ++k) {
     Plan::FClass &F = P.classes[k];
     F.n = (int32_t)F.ids.size();
     F.ncap = kClassCaps[k];
@@ -596,6 +631,10 @@ int activate(pbdr_ctx *c, Plan *P, cudaStream_t s) {
       return rc;
     if (!S->pcontig && (rc = dev_alloc(c, c->s_pmap, npb * 4))) return rc;
     if (!S->bcontig && (rc = dev_alloc(c, c->s_bmap, (size_t)std::max(S->nb, 1) * 4))) return rc;
+    const size_t nbod = (size_t)std::max(c->bcap, 1);
+    if ((rc = dev_alloc(c, c->s_bounds, nbod * 2 * sizeof(float4))) ||
+        (rc = dev_alloc(c, c->s_near, nbod * kNearMax * sizeof(int32_t))))
+      return rc;
   }
   if (!P->tab.empty()) {
     if ((rc = dev_alloc(c, c->tab, P->tab.size() * 4))) return rc;
@@ -650,6 +689,22 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   }
   P.sorted_in_b = in_b;
   StageTimer tm(c, s, 3, launches);
+  // body boxes and near bodies: particles far from every other body skip the search
+  const bool cull = c->s_bounds.bytes >= (size_t)c->bcap * 2 * sizeof(float4) &&
+                    c->s_near.bytes >= (size_t)c->bcap * kNearMax * sizeof(int32_t);
+  if (cull) {
+    BoundArgs ba{};
+    ba.Xp = Xp;
+    ba.quat = c->quat.as<float4>();
+    ba.bodies = c->bodies.as<BodyRec>();
+    ba.scenes = c->scenes.as<ScenePar>();
+    ba.bmap = P.bcontig ? nullptr : c->s_bmap.as<int32_t>();
+    ba.bbase = P.bbase;
+    ba.nbodies = P.nb;
+    ba.bounds = c->s_bounds.as<float4>();
+    ba.near = c->s_near.as<int32_t>();
+    launches += launch_body_bounds(ba, s);
+  }
   // every bucket record to all ones: empty, and the identities of its body minima
   CUDA_TRY(cudaMemsetAsync(c->s_cells.p, 0xFF, (size_t)std::max<uint32_t>(P.T_total, 1) * sizeof(uint4), s));
   const uint32_t *sk = in_b ? c->s_keys_b.as<uint32_t>() : c->s_keys_a.as<uint32_t>();
@@ -681,6 +736,11 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   na.cap = c->nbr_cap;
   na.scene_err = c->scene_err.as<uint32_t>();
   na.np = P.np;
+  if (cull) {
+    na.bounds = c->s_bounds.as<float4>();
+    na.near = c->s_near.as<int32_t>();
+    na.quat = c->quat.as<float4>();
+  }
   launches += launch_neighbors(na, s);
   c->last_nbr_plan = &P;
   return PBDR_OK;
@@ -753,7 +813,7 @@ int launch_class(pbdr_ctx *c, Plan &P, int k, cudaStream_t st) {
 int ensure_class_streams(pbdr_ctx *c) {
   if (c->ev_fork) return PBDR_OK;
   CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNumClasses; ++k) {
     CUDA_TRY(cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming));
   }
@@ -771,6 +831,7 @@ int ensure_tangent(pbdr_ctx *c) {
     int rc = dev_grow(c, *b, bytes, old);
     if (rc) return rc;
     CUDA_TRY(cudaMemset(b->as<unsigned char>() + old, 0, bytes - old));
+    CUDA_TRY(cudaDeviceSynchronize());   // grown rarely; later uploads use other streams
   }
   return PBDR_OK;
 }
@@ -842,6 +903,7 @@ int ensure_adjoint(pbdr_ctx *c) {
     int rc = dev_grow(c, *b, bytes, old);
     if (rc) return rc;
     CUDA_TRY(cudaMemset(b->as<unsigned char>() + old, 0, bytes - old));
+    CUDA_TRY(cudaDeviceSynchronize());   // grown rarely; later uploads use other streams
   }
   return PBDR_OK;
 }
@@ -1129,10 +1191,10 @@ int autotune_fused(pbdr_ctx *c, Plan &P, cudaStream_t s) {
   }
   // guard: keep the tuned shapes only if whole substeps beat the defaults
   if (!todo.empty()) {
-    std::array<Plan::FClass, 4> tuned_shapes = P.classes, defaults = P.classes;
+    std::array<Plan::FClass, kNumClasses> tuned_shapes = P.classes, defaults = P.classes;
     for (int kc : todo)
       if ((rc = default_shape(c, kc, defaults[kc]))) return rc;
-    auto set_shapes = [&](const std::array<Plan::FClass, 4> &src) {
+    auto set_shapes = [&](const std::array<Plan::FClass, kNumClasses> &src) {
       for (int kc : todo) {
         P.classes[kc].threads = src[kc].threads;
         P.classes[kc].grid = src[kc].grid;
@@ -1339,7 +1401,7 @@ int pbdr_ctx_destroy(pbdr_ctx *c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (auto &w : c->work_ev) cudaEventDestroy(w.second);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNumClasses; ++k) {
     if (c->cls_stream[k]) cudaStreamDestroy(c->cls_stream[k]);
     if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
   }
@@ -1374,12 +1436,8 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
       if (cnt <= 0) return fail(PBDR_ERR_INVALID, "body_off must be strictly increasing");
       if (cnt > kMaxBodyParticles) return fail(PBDR_ERR_INVALID, "body too large");
     }
-    for (int32_t p = 0; p < N; ++p) {
-      if (!(d->inv_mass[p] > 0.f) || !std::isfinite(d->inv_mass[p]))
-        return fail(PBDR_ERR_INVALID, "inverse masses must be finite and > 0");
-      if (!finite3(d->pos + 3 * p) || !finite3(d->vel + 3 * p))
-        return fail(PBDR_ERR_INVALID, "positions and velocities must be finite");
-    }
+    // the per-particle checks (finite, inverse mass > 0) run in the
+    // rest-shape pass below, before anything is uploaded
   }
   if ((int64_t)c->pa.top + N > INT32_MAX / 2 || (int64_t)c->ba.top + B > INT32_MAX / 2)
     return fail(PBDR_ERR_INVALID, "context particle or body count overflow");
@@ -1421,53 +1479,115 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     return rc;
   }
 
-  // host-side FP64 rest shape (Mueller et al. 2005): M, c0, q = x0 - c0
-  std::vector<float4> X(N), V(N), Q(N);
-  std::vector<int32_t> pb(N);
+  // Staging of the scene's per-particle arrays in page-locked memory: the
+  // rest-shape pass writes them in place and the upload is a handful of
+  // copies at full link bandwidth.
+  auto al16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
+  const size_t oX = 0, oV = oX + 16 * (size_t)N, oQ = oV + 16 * (size_t)N, oPB = oQ + 16 * (size_t)N;
+  const size_t oBR = al16(oPB + 4 * (size_t)N), oQT = al16(oBR + sizeof(BodyRec) * (size_t)B);
+  const size_t oCM = oQT + 16 * (size_t)B, oWR = oCM + 16 * (size_t)B;
+  const size_t oCK = al16(oWR + sizeof(BodyWrench) * (size_t)B), oOR = al16(oCK + sizeof(Chunk) * chk.size());
+  const size_t oSP = al16(oOR + 4 * (size_t)B), stage_bytes = al16(oSP + sizeof(ScenePar));
+  {
+    const cudaError_t e = c->up_stage.grow(stage_bytes);
+    if (e != cudaSuccess) {
+      give_back();
+      return fail(PBDR_ERR_OOM, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+    }
+  }
+  unsigned char *stage = static_cast<unsigned char *>(c->up_stage.p);
+  float4 *X = reinterpret_cast<float4 *>(stage + oX), *V = reinterpret_cast<float4 *>(stage + oV);
+  float4 *Q = reinterpret_cast<float4 *>(stage + oQ);
+  int32_t *pb = reinterpret_cast<int32_t *>(stage + oPB);
   std::vector<BodyRec> br(B);
   std::vector<float4> com(B);
-  int32_t slot_next = C0;
-  for (int32_t b = 0; b < B; ++b) {
-    const int32_t s0 = d->body_off[b], s1 = d->body_off[b + 1];
-    double M = 0, cx = 0, cy = 0, cz = 0;
-    for (int32_t p = s0; p < s1; ++p) {
-      const double m = 1.0 / (double)d->inv_mass[p];
-      M += m;
-      cx += m * d->pos[3 * p];
-      cy += m * d->pos[3 * p + 1];
-      cz += m * d->pos[3 * p + 2];
+  {
+    int32_t slot_next = C0;
+    for (int32_t b = 0; b < B; ++b) {
+      BodyRec &r = br[b];
+      const int32_t s0 = d->body_off[b], s1 = d->body_off[b + 1];
+      r.slot0 = slot_next;
+      r.nk = (s1 - s0 + kChunk - 1) / kChunk;
+      slot_next += r.nk;
+      r.start = P0 + s0;
+      r.count = s1 - s0;
+      r.scene = sid;
+      r.has_wrench = 0;
     }
-    cx /= M;
-    cy /= M;
-    cz /= M;
-    com[b] = make_float4((float)cx, (float)cy, (float)cz, 0.f);
-    double qs[3] = {0, 0, 0};
-    for (int32_t p = s0; p < s1; ++p) {
-      const float m = (float)(1.0 / (double)d->inv_mass[p]);
-      float4 q = make_float4((float)(d->pos[3 * p] - cx), (float)(d->pos[3 * p + 1] - cy),
-                             (float)(d->pos[3 * p + 2] - cz), m);
-      Q[p] = q;
-      const double md = 1.0 / (double)d->inv_mass[p];
-      qs[0] += md * q.x;
-      qs[1] += md * q.y;
-      qs[2] += md * q.z;
-      X[p] = make_float4(d->pos[3 * p], d->pos[3 * p + 1], d->pos[3 * p + 2], d->inv_mass[p]);
-      V[p] = make_float4(d->vel[3 * p], d->vel[3 * p + 1], d->vel[3 * p + 2], 0.f);
-      pb[p] = B0 + b;
+  }
+  // host-side FP64 rest shape (Mueller et al. 2005): M, c0, q = x0 - c0;
+  // bodies are independent, so large scenes split them over host threads
+  auto rest_pass = [&](int32_t b_begin, int32_t b_end, int *bad) {
+    std::vector<double> mb;   // particle masses of the current body
+    for (int32_t b = b_begin; b < b_end; ++b) {
+      const int32_t s0 = d->body_off[b], s1 = d->body_off[b + 1];
+      mb.resize((size_t)(s1 - s0));
+      double M = 0, cx = 0, cy = 0, cz = 0;
+      for (int32_t p = s0; p < s1; ++p) {
+        const float w = d->inv_mass[p];
+        if (!(w > 0.f) || !std::isfinite(w)) bad[0] = 1;
+        if (!finite3(d->pos + 3 * p) || !finite3(d->vel + 3 * p)) bad[1] = 1;
+        const double m = 1.0 / (double)w;
+        mb[p - s0] = m;
+        M += m;
+        cx += m * d->pos[3 * p];
+        cy += m * d->pos[3 * p + 1];
+        cz += m * d->pos[3 * p + 2];
+      }
+      if (bad[0] || bad[1]) return;
+      cx /= M;
+      cy /= M;
+      cz /= M;
+      com[b] = make_float4((float)cx, (float)cy, (float)cz, 0.f);
+      double qs[3] = {0, 0, 0};
+      for (int32_t p = s0; p < s1; ++p) {
+        const double md = mb[p - s0];
+        const float4 q = make_float4((float)(d->pos[3 * p] - cx), (float)(d->pos[3 * p + 1] - cy),
+                                     (float)(d->pos[3 * p + 2] - cz), (float)md);
+        Q[p] = q;
+        qs[0] += md * q.x;
+        qs[1] += md * q.y;
+        qs[2] += md * q.z;
+        X[p] = make_float4(d->pos[3 * p], d->pos[3 * p + 1], d->pos[3 * p + 2], d->inv_mass[p]);
+        V[p] = make_float4(d->vel[3 * p], d->vel[3 * p + 1], d->vel[3 * p + 2], 0.f);
+        pb[p] = B0 + b;
+      }
+      BodyRec &r = br[b];
+      r.mass = (float)M;
+      r.inv_mass = (float)(1.0 / M);
+      r.qsx = (float)qs[0];
+      r.qsy = (float)qs[1];
+      r.qsz = (float)qs[2];
     }
-    BodyRec &r = br[b];
-    r.slot0 = slot_next;
-    r.nk = (s1 - s0 + kChunk - 1) / kChunk;
-    slot_next += r.nk;
-    r.start = P0 + s0;
-    r.count = s1 - s0;
-    r.scene = sid;
-    r.has_wrench = 0;
-    r.mass = (float)M;
-    r.inv_mass = (float)(1.0 / M);
-    r.qsx = (float)qs[0];
-    r.qsy = (float)qs[1];
-    r.qsz = (float)qs[2];
+  };
+  {
+    const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+    const int nthr = N >= 8192 ? std::max(1, std::min({8, hw, N / 4096})) : 1;
+    std::vector<std::array<int, 2>> bad(nthr, std::array<int, 2>{0, 0});
+    if (nthr == 1) {
+      rest_pass(0, B, bad[0].data());
+    } else {   // contiguous body ranges of about N / nthr particles each
+      std::vector<std::thread> pool;
+      int32_t b_begin = 0;
+      for (int t = 0; t < nthr && b_begin < B; ++t) {
+        const int64_t target = (int64_t)N * (t + 1) / nthr;
+        int32_t b_end = b_begin + 1;
+        while (b_end < B && (t == nthr - 1 || d->body_off[b_end] < target)) ++b_end;
+        pool.emplace_back(rest_pass, b_begin, b_end, bad[t].data());
+        b_begin = b_end;
+      }
+      for (auto &th : pool) th.join();
+    }
+    int bad_mass = 0, bad_finite = 0;
+    for (const auto &f : bad) {
+      bad_mass |= f[0];
+      bad_finite |= f[1];
+    }
+    if (bad_mass || bad_finite) {
+      give_back();
+      return fail(PBDR_ERR_INVALID, bad_mass ? "inverse masses must be finite and > 0"
+                                             : "positions and velocities must be finite");
+    }
   }
   SceneHost S;
   S.alive = true;
@@ -1507,9 +1627,20 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
   P.np = N;
   P.b0 = S.b0;
   P.nb = B;
-  std::vector<float4> quat(B, make_float4(0.f, 0.f, 0.f, 1.f));
   std::vector<BodyWrench> wr(B);
   std::memset(wr.data(), 0, sizeof(BodyWrench) * (size_t)B);
+  // the small per-body and per-scene tables into the staging area too
+  std::memcpy(stage + oBR, br.data(), sizeof(BodyRec) * (size_t)B);
+  for (int32_t b = 0; b < B; ++b) reinterpret_cast<float4 *>(stage + oQT)[b] = make_float4(0.f, 0.f, 0.f, 1.f);
+  std::memcpy(stage + oCM, com.data(), 16 * (size_t)B);
+  std::memcpy(stage + oWR, wr.data(), sizeof(BodyWrench) * (size_t)B);
+  if (!chk.empty()) std::memcpy(stage + oCK, chk.data(), sizeof(Chunk) * chk.size());
+  {  // the scene's bodies, largest first (owner-warp order of the scene-resident kernel)
+    int32_t *ord = reinterpret_cast<int32_t *>(stage + oOR);
+    for (int32_t b = 0; b < B; ++b) ord[b] = B0 + b;
+    std::stable_sort(ord, ord + B, [&](int32_t x, int32_t y) { return br[x - B0].count > br[y - B0].count; });
+  }
+  std::memcpy(stage + oSP, &P, sizeof(ScenePar));
   // device uploads; on failure the taken ranges go back to the free lists
   auto upload = [&]() -> int {
     // a reused scene slot or table range may still be in use by work that was
@@ -1518,44 +1649,41 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
       CUDA_TRY(cudaDeviceSynchronize());
       c->free_dirty = c->work_pending = c->work_unknown = false;
     }
+    // synchronous copies on the legacy stream (measured: the same copies on
+    // a separate non-blocking stream left the tuned substeps 5 % slower)
+    cudaStream_t us = cudaStreamLegacy;
+    auto h2d = [&](void *dst, size_t off, size_t bytes) -> cudaError_t {
+      return bytes ? cudaMemcpy(dst, stage + off, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
     if (N > 0) {
-      CUDA_TRY(cudaMemcpy(c->X[0].as<float4>() + S.p0, X.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->V[0].as<float4>() + S.p0, V.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->Q.as<float4>() + S.p0, Q.data(), (size_t)N * 16, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->pbody.as<int32_t>() + S.p0, pb.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->bodies.as<BodyRec>() + S.b0, br.data(), (size_t)B * sizeof(BodyRec), cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->quat.as<float4>() + S.b0, quat.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->bcom.as<float4>() + S.b0, com.data(), (size_t)B * 16, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(c->wrench.as<BodyWrench>() + S.b0, wr.data(), (size_t)B * sizeof(BodyWrench), cudaMemcpyHostToDevice));
+      CUDA_TRY(h2d(c->X[0].as<float4>() + S.p0, oX, (size_t)N * 16));
+      CUDA_TRY(h2d(c->V[0].as<float4>() + S.p0, oV, (size_t)N * 16));
+      CUDA_TRY(h2d(c->Q.as<float4>() + S.p0, oQ, (size_t)N * 16));
+      CUDA_TRY(h2d(c->pbody.as<int32_t>() + S.p0, oPB, (size_t)N * 4));
+      CUDA_TRY(h2d(c->bodies.as<BodyRec>() + S.b0, oBR, (size_t)B * sizeof(BodyRec)));
+      CUDA_TRY(h2d(c->quat.as<float4>() + S.b0, oQT, (size_t)B * 16));
+      CUDA_TRY(h2d(c->bcom.as<float4>() + S.b0, oCM, (size_t)B * 16));
+      CUDA_TRY(h2d(c->wrench.as<BodyWrench>() + S.b0, oWR, (size_t)B * sizeof(BodyWrench)));
+      CUDA_TRY(h2d(c->border.as<int32_t>() + B0, oOR, (size_t)B * 4));
     }
-    if (!chk.empty())
-      CUDA_TRY(cudaMemcpy(c->chunks.as<Chunk>() + C0, chk.data(), chk.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
-    if (B > 0) {   // the scene's bodies, largest first (owner-warp order of the scene-resident kernel)
-      std::vector<int32_t> ord(B);
-      for (int32_t b = 0; b < B; ++b) ord[b] = B0 + b;
-      std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
-        return br[x - B0].count > br[y - B0].count;
-      });
-      CUDA_TRY(cudaMemcpy(c->border.as<int32_t>() + B0, ord.data(), (size_t)B * 4, cudaMemcpyHostToDevice));
-    }
-    CUDA_TRY(cudaMemcpy(c->scenes.as<ScenePar>() + sid, &P, sizeof(ScenePar), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemset(c->scene_err.as<uint32_t>() + sid, 0, 4));
+    CUDA_TRY(h2d(c->chunks.as<Chunk>() + C0, oCK, chk.size() * sizeof(Chunk)));
+    CUDA_TRY(h2d(c->scenes.as<ScenePar>() + sid, oSP, sizeof(ScenePar)));
+    CUDA_TRY(cudaMemsetAsync(c->scene_err.as<uint32_t>() + sid, 0, 4, us));
     if (c->dmu.p && (size_t)(sid + 1) * 4 <= c->dmu.bytes)
-      CUDA_TRY(cudaMemset(c->dmu.as<float>() + sid, 0, 4));
+      CUDA_TRY(cudaMemsetAsync(c->dmu.as<float>() + sid, 0, 4, us));
     if (c->Xb[0].p && N > 0) {   // adjoints in use: the new scene starts with zero adjoints
       if ((rc = ensure_adjoint(c))) return rc;
       for (DevBuf *b : {&c->Xb[0], &c->Xb[1], &c->Vb[0], &c->Vb[1], &c->Ub})
-        CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
+        CUDA_TRY(cudaMemsetAsync(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4), us));
     }
     if (c->Xd[0].p && N > 0) {   // tangents in use: the new scene starts with zero tangents
       if ((rc = ensure_tangent(c))) return rc;
       for (DevBuf *b : {&c->Xd[0], &c->Xd[1], &c->Vd[0], &c->Vd[1]})
-        CUDA_TRY(cudaMemset(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4)));
+        CUDA_TRY(cudaMemsetAsync(b->as<float4>() + S.p0, 0, (size_t)N * sizeof(float4), us));
     }
-    // the copies from pageable host memory and the memsets above run on the
-    // legacy default stream, which work on non-blocking streams does not wait
-    // for: complete them before returning
-    CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
+    // complete the uploads and memsets before returning: later work on any
+    // stream then sees them, and the staging area may be reused by the next call
+    CUDA_TRY(cudaStreamSynchronize(us));
     return PBDR_OK;
   };
   if ((rc = upload())) {
@@ -2059,11 +2187,12 @@ int pbdr_set_option(pbdr_ctx *c, int32_t option, int64_t value) {
 
 int pbdr_plan_config(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t *out, int32_t cap) {
   g_err.clear();
-  if (!c || !out || cap < 20) return fail(PBDR_ERR_INVALID, "need an output array of 20 int32");
+  if (!c || !out || cap < 5 * kNumClasses)
+    return fail(PBDR_ERR_INVALID, "need an output array of " + std::to_string(5 * kNumClasses) + " int32");
   Plan *P = nullptr;
   int rc = build_plan(c, ids, n, &P);
   if (rc) return rc;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNumClasses; ++k) {
     const bool has = P->fused;
     out[5 * k + 0] = has ? P->classes[k].ncap : 0;
     out[5 * k + 1] = has ? P->classes[k].n : 0;

@@ -53,7 +53,6 @@ __device__ __forceinline__ float d2rn(float3 p, float3 q) {
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-constexpr int kNearMax = 8;   // near bodies kept per body; more marks every particle interface
 
 // u16 array lengths are padded to a multiple of 8 so the next array stays 16-byte aligned
 __device__ __forceinline__ int ncap_even(int n) { return (n + 7) & ~7; }

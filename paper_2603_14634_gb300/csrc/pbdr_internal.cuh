@@ -21,6 +21,7 @@ constexpr uint32_t kSceneHasWrench = 1u << 16;
 
 constexpr uint32_t kEmptyCell = 0xFFFFFFFFu;
 constexpr int kFusedNbrCap = 32;    // neighbour slots per particle in the fused kernel
+constexpr int kNearMax = 8;         // near bodies kept per body; more: every particle is searched
 constexpr int kFusedBodyCap = 64;   // bodies per scene whose rotation / anchor sit in shared memory
 constexpr int kMaxBodyParticles = 1 << 20;
 
@@ -114,6 +115,24 @@ struct NbrArgs {
   int32_t cap;
   uint32_t *scene_err;
   int32_t np;
+  // culling (nullptr: search every particle): per body its bounding box
+  // (2 float4: centre and sphere radius, half-extents and near-body count),
+  // its near bodies (kNearMax ids) and its warm-start rotation
+  const float4 *bounds;
+  const int32_t *near;
+  const float4 *quat;
+};
+
+// per-body bounding boxes and near-body lists of the streaming neighbour stage
+struct BoundArgs {
+  const float4 *Xp;        // predicted positions
+  const float4 *quat;      // warm-start rotations (box frames)
+  const BodyRec *bodies;
+  const ScenePar *scenes;
+  const int32_t *bmap;     // plan body -> global body (nullptr: bbase + i)
+  int32_t bbase, nbodies;
+  float4 *bounds;          // [2 per body]
+  int32_t *near;           // [kNearMax per body]
 };
 
 struct IterArgs {
@@ -225,6 +244,7 @@ struct PackArgs {
 int launch_predict(const PredictArgs &a, cudaStream_t s);
 int launch_cells(const CellArgs &a, cudaStream_t s);
 int launch_neighbors(const NbrArgs &a, cudaStream_t s);
+int launch_body_bounds(const BoundArgs &a, cudaStream_t s);
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_iterate_tangent(const IterArgs &a, const TangentArgs &t, cudaStream_t s);
 int launch_predict_tangent(const TangentPredictArgs &a, cudaStream_t s);

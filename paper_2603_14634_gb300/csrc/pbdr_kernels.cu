@@ -40,6 +40,12 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
 // ---- hashed uniform grid (FP32, round-to-nearest, no contraction) --------
 
 __device__ __forceinline__ int32_t cell_coord(float x, float inv_h) {
@@ -124,6 +130,78 @@ __global__ void __launch_bounds__(256) k_cells(CellArgs a) {
 
 constexpr int kNbrCapMax = 64;
 
+// Bounding box of every body of the plan on its predicted positions, in the
+// frame of its warm-start rotation, grown for rounding, and its bounding
+// sphere (one warp per body).
+__global__ void __launch_bounds__(128) k_body_bounds(BoundArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.nbodies) return;
+  const int32_t b = a.bmap ? a.bmap[w] : a.bbase + w;
+  const BodyRec br = a.bodies[b];
+  const int32_t p0 = br.start, pe = br.start + br.count;
+  const float3 o = f3(a.Xp[p0]);
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 x = a.Xp[p];
+    sx += x.x - o.x;
+    sy += x.y - o.y;
+    sz += x.z - o.z;
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  sz = warp_sum(sz);
+  const float inv = 1.f / (float)br.count;
+  const float3 cen = make_float3(o.x + sx * inv, o.y + sy * inv, o.z + sz * inv);
+  float R[9];
+  quat_to_mat(a.quat[b], R);
+  float ex = 0.f, ey = 0.f, ez = 0.f;
+  for (int32_t p = p0 + lane; p < pe; p += 32) {
+    const float4 x = a.Xp[p];
+    const float dx = x.x - cen.x, dy = x.y - cen.y, dz = x.z - cen.z;
+    ex = fmaxf(ex, fabsf(R[0] * dx + R[3] * dy + R[6] * dz));
+    ey = fmaxf(ey, fabsf(R[1] * dx + R[4] * dy + R[7] * dz));
+    ez = fmaxf(ez, fabsf(R[2] * dx + R[5] * dy + R[8] * dz));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ex = fmaxf(ex, __shfl_xor_sync(kFull, ex, off));
+    ey = fmaxf(ey, __shfl_xor_sync(kFull, ey, off));
+    ez = fmaxf(ez, __shfl_xor_sync(kFull, ez, off));
+  }
+  if (lane == 0) {
+    float3 e = make_float3(ex, ey, ez);
+    const float rad = cull_box_grow(e, cen);
+    a.bounds[2 * (int64_t)b] = make_float4(cen.x, cen.y, cen.z, rad);
+    a.bounds[2 * (int64_t)b + 1] = make_float4(e.x, e.y, e.z, 0.f);
+  }
+}
+
+// Near bodies of every body of the plan (bounding spheres within R_n of each
+// other, same scene); the count goes to bounds[2 b + 1].w, the first
+// kNearMax ids to near[kNearMax b ...].  One thread per body.
+__global__ void __launch_bounds__(128) k_near_bodies(BoundArgs a) {
+  const int32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= a.nbodies) return;
+  const int32_t b = a.bmap ? a.bmap[w] : a.bbase + w;
+  const BodyRec br = a.bodies[b];
+  const ScenePar sp = a.scenes[br.scene];
+  const float reach = cull_reach(sp.Rn2);
+  const float4 sa = a.bounds[2 * (int64_t)b];
+  int nn = 0;
+  for (int32_t bo = sp.b0; bo < sp.b0 + sp.nb; ++bo) {
+    if (bo == b) continue;
+    const float4 sb = a.bounds[2 * (int64_t)bo];
+    if (cull_spheres_near(f3(sa), sa.w, f3(sb), sb.w, reach)) {
+      if (nn < kNearMax) a.near[(int64_t)kNearMax * b + nn] = bo;
+      ++nn;
+    }
+  }
+  float4 e = a.bounds[2 * (int64_t)b + 1];
+  e.w = __int_as_float(nn);
+  a.bounds[2 * (int64_t)b + 1] = e;
+}
+
 __global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
   // threads walk the particles in caller order: the particles of a body are
   // contiguous and close in space, so a warp's bucket lookups coincide
@@ -134,6 +212,26 @@ __global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
   const int32_t bp = a.pbody[p];
   const int32_t s = a.bodies[bp].scene;
   const ScenePar sp = a.scenes[s];
+  if (a.bounds) {
+    // a particle farther than R_n from the box of every body near its own
+    // has no neighbour: skip the 27-cell search
+    const int nn = __float_as_int(a.bounds[2 * (int64_t)bp + 1].w);
+    if (nn <= kNearMax) {
+      const float reach = cull_reach(sp.Rn2);
+      bool iface = false;
+      for (int k = 0; k < nn && !iface; ++k) {
+        const int32_t bo = a.near[(int64_t)kNearMax * bp + k];
+        const float4 c4 = a.bounds[2 * (int64_t)bo], e4 = a.bounds[2 * (int64_t)bo + 1];
+        float R[9];
+        quat_to_mat(a.quat[bo], R);
+        iface = cull_near_box(f3(xp), f3(c4), f3(e4), R, reach);
+      }
+      if (!iface) {
+        a.nbr_cnt[p] = 0;
+        return;
+      }
+    }
+  }
   const uint32_t hb = a.hbase[s], mask = sp.T - 1u;
   const int32_t ix = cell_coord(xp.x, sp.inv_h), iy = cell_coord(xp.y, sp.inv_h),
                 iz = cell_coord(xp.z, sp.inv_h);
@@ -178,11 +276,6 @@ __global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
   if (cnt > cap) atomicOr(&a.scene_err[s], (uint32_t)PBDR_EBIT_NBR_OVERFLOW);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 // ---------------------------------------------------------------------------
 // contact corrections of one particle (Sec. III-A constraints (1), (2)):
@@ -1121,6 +1214,13 @@ int launch_cells(const CellArgs &a, cudaStream_t s) {
   if (a.np <= 0) return 0;
   k_cells<<<blocks_for(a.np, 256), 256, 0, s>>>(a);
   return 1;
+}
+
+int launch_body_bounds(const BoundArgs &a, cudaStream_t s) {
+  if (a.nbodies <= 0) return 0;
+  k_body_bounds<<<(a.nbodies + 3) / 4, 128, 0, s>>>(a);
+  k_near_bodies<<<(a.nbodies + 127) / 128, 128, 0, s>>>(a);
+  return 2;
 }
 
 int launch_neighbors(const NbrArgs &a, cudaStream_t s) {

@@ -301,5 +301,46 @@ __device__ __forceinline__ void momentum_step(const float *s, float3 cA, float M
   }
 }
 
+// ---------------------------------------------------------------------------
+// Exact culling of the neighbour search.  A particle p can only be within R_n
+// of a particle of body B if it lies within R_n of B's bounding box.  Every
+// test below carries a margin that covers the FP32 rounding of the frame
+// change and of |R| != 1, so culling never drops a pair of the O(N^2)
+// definition.
+// ---------------------------------------------------------------------------
+
+// the search reach R_n with its rounding margin
+__device__ __forceinline__ float cull_reach(float Rn2) { return sqrtf(Rn2) * (1.f + 1e-5f) + 1e-6f; }
+
+// grows the box half-extents e of a body (centre cen) for rounding; returns
+// the radius of its bounding sphere
+__device__ __forceinline__ float cull_box_grow(float3 &e, float3 cen) {
+  const float g = 1e-5f * (e.x + e.y + e.z + fabsf(cen.x) + fabsf(cen.y) + fabsf(cen.z)) + 1e-6f;
+  e.x += g;
+  e.y += g;
+  e.z += g;
+  return sqrtf(e.x * e.x + e.y * e.y + e.z * e.z) * (1.f + 1e-5f) + 1e-6f;
+}
+
+// bodies a (sphere centre ca, radius ra) and b may hold a pair within R_n
+__device__ __forceinline__ bool cull_spheres_near(float3 ca, float ra, float3 cb, float rb, float reach) {
+  const float3 d = make_float3(ca.x - cb.x, ca.y - cb.y, ca.z - cb.z);
+  const float lim = ra + rb + reach +
+                    1e-5f * (fabsf(ca.x) + fabsf(ca.y) + fabsf(ca.z) + fabsf(cb.x) + fabsf(cb.y) + fabsf(cb.z) + ra + rb) +
+                    1e-6f;
+  return d.x * d.x + d.y * d.y + d.z * d.z <= lim * lim;
+}
+
+// particle x lies within R_n of the box (centre cen, half-extents e, axes the
+// columns of R) of another body
+__device__ __forceinline__ bool cull_near_box(float3 x, float3 cen, float3 e, const float *R, float reach) {
+  const float3 d = make_float3(x.x - cen.x, x.y - cen.y, x.z - cen.z);
+  const float ux = fmaxf(fabsf(R[0] * d.x + R[3] * d.y + R[6] * d.z) - e.x, 0.f);
+  const float uy = fmaxf(fabsf(R[1] * d.x + R[4] * d.y + R[7] * d.z) - e.y, 0.f);
+  const float uz = fmaxf(fabsf(R[2] * d.x + R[5] * d.y + R[8] * d.z) - e.z, 0.f);
+  const float lim = reach + 1e-5f * (fabsf(d.x) + fabsf(d.y) + fabsf(d.z)) + 1e-6f;
+  return ux * ux + uy * uy + uz * uz <= lim * lim;
+}
+
 }  // namespace
 }  // namespace pbdr

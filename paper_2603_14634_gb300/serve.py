@@ -107,6 +107,9 @@ class Server:
         self.results: Dict[int, tuple] = {}
         self.ledger = 0
         self.event_factory = event_factory
+        # finished states are read back into page-locked host buffers (grow-only)
+        self._pinned = ctx_factory is None
+        self._pin_pos = self._pin_vel = None
         self._inflight: collections.deque = collections.deque()   # (start, end) events per tick
         self.tick_ms: List[float] = []
         self.host_ms = {"admit": 0.0, "step": 0.0, "retire": 0.0}
@@ -164,12 +167,23 @@ class Server:
         done = self._due.pop(self._stepped, [])   # in admission order
         if not done:
             return
-        pos, vel, err = self.ctx.read_states([r.sid for r in done], stream=self.stream)
+        ids = [r.sid for r in done]
+        if self._pinned:
+            total = sum(int(r.scene.num_particles) for r in done)
+            if self._pin_pos is None or self._pin_pos.shape[0] < total:
+                import torch
+                cap = max(total, 2 * (0 if self._pin_pos is None else self._pin_pos.shape[0]))
+                self._pin_pos = torch.empty((cap, 3), dtype=torch.float32, pin_memory=True).numpy()
+                self._pin_vel = torch.empty((cap, 3), dtype=torch.float32, pin_memory=True).numpy()
+            pos, vel = self._pin_pos[:total], self._pin_vel[:total]
+            _, _, err = self.ctx.read_states(ids, pos, vel, stream=self.stream)
+        else:
+            pos, vel, err = self.ctx.read_states(ids, stream=self.stream)
         now = self.clock() - self.t0              # the results are on the host now
         at = 0
         for k, req in enumerate(done):
             n = int(req.scene.num_particles)
-            self.results[req.rid] = (pos[at:at + n], vel[at:at + n], int(err[k]))
+            self.results[req.rid] = (pos[at:at + n].copy(), vel[at:at + n].copy(), int(err[k]))
             at += n
             self.ctx.destroy_scene(req.sid)
             self.ledger -= self._cost(req)

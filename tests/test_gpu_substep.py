@@ -252,10 +252,11 @@ def test_determinism_and_batch_invariance(pbdr_lib, streaming):
 
 def test_mixed_sizes_every_class_and_streaming_rest(ctx, orc):
     """One batch holding scenes of every size class of the scene-resident
-    kernel (<= 1024, 2048, 4096, 8192 particles) and one larger scene that
-    the streaming kernels take, one substep from oracle-evolved states."""
+    kernel (<= 1024, 2048, 4096, 8192 particles; the smallest class with
+    scenes of 250 to 750 particles) and one larger scene that the streaming
+    kernels take, one substep from oracle-evolved states."""
     scs = [scenes.random_bodies_scene(seed=s, num_bodies=nb) for s, nb in
-           ((10, 6), (11, 14), (12, 30), (13, 60), (14, 80))]   # 750 .. 10000 particles
+           ((8, 2), (9, 4), (10, 6), (11, 14), (12, 30), (13, 60), (14, 80))]   # 250 .. 10000 particles
     states = []
     for sc in scs:
         sc.pos = (sc.pos * np.float32(0.85)).astype(np.float32)
