@@ -152,6 +152,7 @@ struct Plan {
   // nseg + 1 segment starts (plan index) followed by nseg global bases
   std::vector<int32_t> tab;
   int32_t o_hbase = -1, o_wlist = -1, o_pseg = -1, o_bseg = -1, nseg = 0;
+  int32_t o_iorder = -1;           // streaming solver iterations: body order (global ids)
   // scene-resident form: size classes of scenes, each one persistent launch
   bool fused = false;
   struct FClass {
@@ -494,6 +495,28 @@ int fill_stream_plan(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, Plan &P, std
     P.o_bseg = (int32_t)tab.size();
     tab.insert(tab.end(), bstart.begin(), bstart.end());
     tab.insert(tab.end(), bb0.begin(), bb0.end());
+  }
+  {  // solver-iteration order: bodies by size bucket (floor of log2 of the
+     // particle count), largest first, so that each launch ends on small
+     // bodies (a counting sort: linear in the bodies of the plan)
+    auto bucket = [&](int32_t b) { return 31 - __builtin_clz((unsigned)std::max(c->bh[b].count, 1)); };
+    int32_t at[33] = {0};
+    for (int32_t i = 0; i < n; ++i) {
+      const SceneHost &S = c->sh[ids[i]];
+      for (int32_t b = S.b0; b < S.b0 + S.nb; ++b) ++at[bucket(b)];
+    }
+    for (int32_t k = 32, run = 0; k >= 0; --k) {
+      const int32_t m = at[k];
+      at[k] = run;
+      run += m;
+    }
+    P.o_iorder = (int32_t)tab.size();
+    tab.resize(tab.size() + P.nb);
+    int32_t *o = tab.data() + P.o_iorder;
+    for (int32_t i = 0; i < n; ++i) {
+      const SceneHost &S = c->sh[ids[i]];
+      for (int32_t b = S.b0; b < S.b0 + S.nb; ++b) o[at[bucket(b)]++] = b;
+    }
   }
   if (!P.wrench_list.empty()) {
     P.o_wlist = (int32_t)tab.size();
@@ -1290,7 +1313,7 @@ int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   ia.scenes = c->scenes.as<ScenePar>();
   ia.quat = c->quat.as<float4>();
   ia.bcom = c->bcom.as<float4>();
-  ia.bmap = P.bcontig ? nullptr : c->s_bmap.as<int32_t>();
+  ia.bmap = c->tab.as<int32_t>() + P.o_iorder;   // bodies largest first
   ia.bbase = P.bbase;
   ia.nbodies = P.nb;
   ia.scene_err = c->scene_err.as<uint32_t>();
@@ -1301,7 +1324,7 @@ int substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
     ia.Xout = out ? X1 : X0;
     ia.Vout = out ? V1 : V0;
     ia.k = k;
-    launches += launch_iterate(ia, 4, s);
+    launches += launch_iterate(ia, 1, s);   // one-warp CTAs: a finished body frees its slot at once
   }
   CUDA_TRY(cudaGetLastError());
   return PBDR_OK;

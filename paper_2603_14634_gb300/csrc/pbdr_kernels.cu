@@ -17,6 +17,8 @@
 //               momentum enforcement -> X_{i+1}, V_{i+1}
 #include <math.h>
 
+#include <algorithm>
+
 #include "pbdr_internal.cuh"
 #include "pbdr_math.cuh"
 
@@ -1231,8 +1233,8 @@ int launch_neighbors(const NbrArgs &a, cudaStream_t s) {
 
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s) {
   if (a.nbodies <= 0) return 0;
-  (void)warps_per_block;
-  k_iterate<<<blocks_for(a.nbodies, 4), 128, 0, s>>>(a);
+  const int wpb = std::max(1, std::min(4, warps_per_block));
+  k_iterate<<<blocks_for(a.nbodies, wpb), 32 * wpb, 0, s>>>(a);
   return 1;
 }
 
