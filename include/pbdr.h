@@ -155,6 +155,19 @@ int pbdr_read_states(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, float *pos
 int pbdr_write_states(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n,
                       const float *pos, const float *vel, void *stream);
 
+/* pbdr_read_states without the final synchronisation: enqueues the gather
+ * and the copies on `stream` and returns.  pos, vel and err_bits are valid
+ * once the stream has reached this point (an event recorded after the call,
+ * or a stream sync); page-locked host buffers keep the copies asynchronous
+ * (pageable ones make them wait for the stream).  The device staging area is
+ * shared with the other reads and writes of states, so issue those on the
+ * same stream or after this read has completed.  A scene read this way
+ * counts as in use until the read completes: destroying it earlier makes
+ * the next scene that reuses its ranges wait for the device.  Serving uses
+ * it to read finished requests between two substeps on one stream. */
+int pbdr_read_states_async(pbdr_ctx *ctx, const pbdr_scene *ids, int32_t n, float *pos,
+                           float *vel, uint32_t *err_bits, void *stream);
+
 /* Number of particles and bodies of a scene (either pointer may be NULL). */
 int pbdr_scene_info(pbdr_ctx *ctx, pbdr_scene scene, int32_t *num_particles,
                     int32_t *num_bodies);

@@ -27,7 +27,7 @@ EBIT_NONFINITE = 2
 EXPORTS = [
     "pbdr_ctx_create", "pbdr_ctx_destroy", "pbdr_create_scene", "pbdr_destroy_scene",
     "pbdr_set_body_wrench", "pbdr_step", "pbdr_read_state", "pbdr_write_state",
-    "pbdr_read_states", "pbdr_write_states", "pbdr_scene_info", "pbdr_last_error",
+    "pbdr_read_states", "pbdr_read_states_async", "pbdr_write_states", "pbdr_scene_info", "pbdr_last_error",
     "pbdr_build_neighbors", "pbdr_read_neighbors", "pbdr_last_launch_count",
     "pbdr_neighbor_total", "pbdr_set_profiling", "pbdr_read_profile",
     "pbdr_neighbors_noalloc", "pbdr_set_option", "pbdr_plan_config",
@@ -89,6 +89,7 @@ def load(path: Optional[str] = None):
     L.pbdr_read_state.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pbdr_write_state.argtypes = [vp, i32, vp, vp, vp]
     L.pbdr_read_states.argtypes = [vp, P(i32), i32, vp, vp, vp, vp]
+    L.pbdr_read_states_async.argtypes = [vp, P(i32), i32, vp, vp, vp, vp]
     L.pbdr_write_states.argtypes = [vp, P(i32), i32, vp, vp, vp]
     L.pbdr_step_tangent.argtypes = [vp, P(i32), i32, i32, vp]
     L.pbdr_write_tangent.argtypes = [vp, i32, vp, vp, vp]
@@ -287,6 +288,13 @@ def pbdr_read_states(ctx: int, ids: Sequence[int], pos=None, vel=None, stream=No
     return pos, vel, err
 
 
+def pbdr_read_states_async(ctx: int, ids: Sequence[int], pos, vel, err, stream=None) -> None:
+    """Enqueues a batched read into caller-owned host buffers (page-locked
+    for an asynchronous copy); they are valid once the stream reaches it."""
+    arr, p = _ids(ids)
+    _check(load().pbdr_read_states_async(ctx, p, len(arr), _ptr(pos), _ptr(vel), _ptr(err), _stream(stream)))
+
+
 def pbdr_write_states(ctx: int, ids: Sequence[int], pos=None, vel=None, stream=None) -> None:
     arr, p = _ids(ids)
     _check(load().pbdr_write_states(ctx, p, len(arr), _ptr(pos), _ptr(vel), _stream(stream)))
@@ -409,6 +417,9 @@ class Context:
 
     def read_states(self, ids, pos=None, vel=None, stream=None):
         return pbdr_read_states(self.h, ids, pos, vel, stream)
+
+    def read_states_async(self, ids, pos, vel, err, stream=None):
+        pbdr_read_states_async(self.h, ids, pos, vel, err, stream)
 
     def write_states(self, ids, pos=None, vel=None, stream=None):
         pbdr_write_states(self.h, ids, pos, vel, stream)

@@ -35,7 +35,6 @@ int fail(int code, const std::string &msg) {
                   std::string(#expr) + ": " + cudaGetErrorString(e_));              \
   } while (0)
 
-// owned device allocation
 // page-locked host memory (grow-only staging for uploads)
 struct PinnedBuf {
   void *p = nullptr;
@@ -61,6 +60,26 @@ struct PinnedBuf {
   }
 };
 
+// Page-locked staging for the small host-to-device tables of a call (plan
+// tables, segment tables, scene ids), used round-robin: a copy from pageable
+// memory may make the driver synchronise with the stream it is issued on,
+// which would hold the host until earlier work there (a substep) finishes.
+// A slot is reused once the copy that last read it has completed.
+struct StageRing {
+  static constexpr int kSlots = 8;
+  PinnedBuf buf[kSlots];
+  cudaEvent_t ev[kSlots] = {};
+  int next = 0;
+  StageRing() = default;
+  StageRing(const StageRing &) = delete;
+  StageRing &operator=(const StageRing &) = delete;
+  ~StageRing() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+// owned device allocation
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
@@ -125,6 +144,7 @@ struct SceneHost {
   ScenePar par{};
   int wrench_bodies = 0;
   int32_t c0 = 0, nc = 0;          // chunk range
+  uint64_t last_step = 0;          // sequence number of the last step or asynchronous read of it (0: none)
 };
 
 // A step plan: the host-side description of one batched substep over a list
@@ -134,6 +154,7 @@ struct SceneHost {
 // active one; the streaming form's sort and cell scratch is the context's.
 // size classes of the scene-resident kernel (particle capacities below)
 constexpr int kNumClasses = 4;
+constexpr int kStepRing = 64;      // step events kept for the per-scene idle test
 
 struct Plan {
   std::vector<int32_t> ids;
@@ -208,6 +229,11 @@ struct pbdr_ctx {
   bool work_pending = false;   // some recorded work may not have completed
   bool work_unknown = false;   // an event could not be recorded: assume work in flight
   bool free_dirty = false;     // freed ranges may still be used by work in flight
+  bool async_other = false;    // a call other than pbdr_step may have left work in flight
+  // one event per pbdr_step call, recorded after its work, in a ring: a
+  // scene whose last step's event has completed is no longer in use
+  uint64_t step_seq = 0;
+  cudaEvent_t step_ev[kStepRing] = {};
   size_t budget = 0;
   size_t used = 0;
   int32_t pcap = 0, bcap = 0, scap = 0;
@@ -248,6 +274,7 @@ struct pbdr_ctx {
   DevBuf stage_pos, stage_vel, seg_p0, seg_off, err_ids, err_out;
   // scene uploads: pinned staging
   PinnedBuf up_stage;
+  StageRing h2d_ring;              // small tables of other calls
   // stage profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -284,6 +311,24 @@ void dev_free(pbdr_ctx *c, DevBuf &b) {
   if (b.p) ++c->gen;
   c->used -= b.bytes;
   b.release();
+}
+
+// copies `bytes` from host memory `src` (any kind) to device memory `dst`
+// on stream s through the next slot of the staging ring
+int staged_h2d(pbdr_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return PBDR_OK;
+  StageRing &R = c->h2d_ring;
+  const int k = R.next;
+  R.next = (k + 1) % StageRing::kSlots;
+  if (R.ev[k])
+    CUDA_TRY(cudaEventSynchronize(R.ev[k]));   // the slot's last copy has read it
+  else
+    CUDA_TRY(cudaEventCreateWithFlags(&R.ev[k], cudaEventDisableTiming));
+  CUDA_TRY(R.buf[k].grow(bytes));
+  std::memcpy(R.buf[k].p, src, bytes);
+  CUDA_TRY(cudaMemcpyAsync(dst, R.buf[k].p, bytes, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaEventRecord(R.ev[k], s));
+  return PBDR_OK;
 }
 
 // records that library work was enqueued on stream s
@@ -334,14 +379,49 @@ bool work_done(pbdr_ctx *c) {
   return true;
 }
 
-// notes, when a call that took a stream returns, the work it enqueued there
+// notes, when a call that took a stream returns, the work it enqueued there;
+// a call whose work is complete when it returns (a read that synchronises)
+// or that stamped its scenes (a step) sets `quiet`
 struct WorkNote {
   pbdr_ctx *c;
   cudaStream_t s;
+  bool quiet = false;
   ~WorkNote() {
-    if (c) note_work(c, s);
+    if (!c) return;
+    note_work(c, s);
+    if (!quiet) c->async_other = true;
   }
 };
+
+// after a successful pbdr_step (or asynchronous read) on stream s: records
+// the call's event and stamps its scenes with the call's sequence number
+void stamp_use(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, cudaStream_t s) {
+  const uint64_t seq = ++c->step_seq;
+  cudaEvent_t &e = c->step_ev[seq % kStepRing];
+  if ((!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) ||
+      cudaEventRecord(e, s) != cudaSuccess) {
+    cudaGetLastError();
+    c->async_other = true;   // the scenes' stamps would be stale: fall back to the global test
+    return;
+  }
+  for (int32_t i = 0; i < n; ++i) c->sh[ids[i]].last_step = seq;
+}
+
+// true when no work enqueued by an earlier call can still touch the ranges
+// of scene S (queries, never waits): its last step has completed and every
+// other call's work has too
+bool scene_idle(pbdr_ctx *c, const SceneHost &S) {
+  if (c->async_other) {
+    if (!work_done(c)) return false;
+    c->async_other = false;
+  }
+  if (S.last_step == 0) return true;
+  if (c->step_seq - S.last_step >= (uint64_t)kStepRing) return work_done(c);   // its event was reused
+  const cudaError_t q = cudaEventQuery(c->step_ev[S.last_step % kStepRing]);
+  if (q == cudaSuccess) return true;
+  if (q != cudaErrorNotReady) cudaGetLastError();
+  return false;
+}
 
 // grow `b` to `bytes`, keeping the first `keep` bytes
 int dev_grow(pbdr_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
@@ -661,7 +741,7 @@ int activate(pbdr_ctx *c, Plan *P, cudaStream_t s) {
   }
   if (!P->tab.empty()) {
     if ((rc = dev_alloc(c, c->tab, P->tab.size() * 4))) return rc;
-    CUDA_TRY(cudaMemcpyAsync(c->tab.p, P->tab.data(), P->tab.size() * 4, cudaMemcpyHostToDevice, s));
+    if ((rc = staged_h2d(c, c->tab.p, P->tab.data(), P->tab.size() * 4, s))) return rc;
   }
   if (S && S->np > 0) {
     const int32_t *t = c->tab.as<int32_t>();
@@ -1340,7 +1420,7 @@ __global__ void k_errs(uint32_t *scene_err, const int32_t *ids, int32_t n, uint3
 // gather / scatter of xyz state for scenes ids[0..n) through device staging
 int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, float *hvel,
                     const float *cpos, const float *cvel, uint32_t *err_bits, int unpack,
-                    cudaStream_t s, float4 *bufX = nullptr, float4 *bufV = nullptr) {
+                    cudaStream_t s, float4 *bufX = nullptr, float4 *bufV = nullptr, bool sync = true) {
   if (!c) return fail(PBDR_ERR_INVALID, "NULL context");
   if (!ids || n < 1) return fail(PBDR_ERR_INVALID, "need at least one scene id");
   std::vector<int32_t> p0(n);
@@ -1359,8 +1439,8 @@ int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, 
   if ((rc = dev_alloc(c, c->seg_off, (size_t)(n + 1) * 8))) return rc;
   if (want_pos && (rc = dev_alloc(c, c->stage_pos, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
   if (want_vel && (rc = dev_alloc(c, c->stage_vel, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
-  CUDA_TRY(cudaMemcpyAsync(c->seg_p0.p, p0.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->seg_off.p, off.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
+  if ((rc = staged_h2d(c, c->seg_p0.p, p0.data(), (size_t)n * 4, s))) return rc;
+  if ((rc = staged_h2d(c, c->seg_off.p, off.data(), (size_t)(n + 1) * 8, s))) return rc;
   PackArgs pa{};
   pa.X = bufX ? bufX : c->X[0].as<float4>();
   pa.V = bufV ? bufV : c->V[0].as<float4>();
@@ -1383,13 +1463,13 @@ int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, 
   if (err_bits) {
     if ((rc = dev_alloc(c, c->err_ids, (size_t)n * 4))) return rc;
     if ((rc = dev_alloc(c, c->err_out, (size_t)n * 4))) return rc;
-    CUDA_TRY(cudaMemcpyAsync(c->err_ids.p, ids, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    if ((rc = staged_h2d(c, c->err_ids.p, ids, (size_t)n * 4, s))) return rc;
     k_errs<<<(n + 255) / 256, 256, 0, s>>>(c->scene_err.as<uint32_t>(), c->err_ids.as<int32_t>(), n,
                                             c->err_out.as<uint32_t>());
     CUDA_TRY(cudaMemcpyAsync(err_bits, c->err_out.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   }
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaStreamSynchronize(s));
+  if (sync) CUDA_TRY(cudaStreamSynchronize(s));
   return PBDR_OK;
 }
 
@@ -1422,6 +1502,8 @@ int pbdr_ctx_destroy(pbdr_ctx *c) {
   cudaDeviceSynchronize();
   invalidate_plans(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->step_ev)
+    if (e) cudaEventDestroy(e);
   for (auto &w : c->work_ev) cudaEventDestroy(w.second);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (int k = 0; k < kNumClasses; ++k) {
@@ -1742,11 +1824,12 @@ int pbdr_destroy_scene(pbdr_ctx *c, pbdr_scene s) {
   g_err.clear();
   int rc = check_scene(c, s);
   if (rc) return rc;
-  // the ranges freed here are clean once every call's work has completed
-  // (e.g. after a read of the results); otherwise the next call that reuses
-  // a freed range waits for the device first
-  c->free_dirty = !work_done(c);
+  // the ranges freed here are clean when the scene's last step and every
+  // other call's work have completed (e.g. after a read of its results),
+  // even while steps of other scenes run; otherwise the next call that
+  // reuses a freed range waits for the device first
   SceneHost &S = c->sh[s];
+  c->free_dirty = work_done(c) ? false : (c->free_dirty || !scene_idle(c, S));
   S.alive = false;
   c->pa.give(S.p0, S.np);
   c->ba.give(S.b0, S.nb);
@@ -1823,6 +1906,8 @@ int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, v
     }
   }
   c->last_launches = launches;
+  stamp_use(c, ids, n, s);
+  work_note.quiet = true;
   return PBDR_OK;
 }
 
@@ -1838,7 +1923,9 @@ int pbdr_read_state(pbdr_ctx *c, pbdr_scene s, float *pos, float *vel, uint32_t 
     }
     return PBDR_OK;
   }
-  return transfer_states(c, &s, 1, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
+  rc = transfer_states(c, &s, 1, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
+  work_note.quiet = rc == PBDR_OK;   // the read synchronised its stream
+  return rc;
 }
 
 int pbdr_write_state(pbdr_ctx *c, pbdr_scene s, const float *pos, const float *vel, void *stream) {
@@ -1854,7 +1941,22 @@ int pbdr_read_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *pos, 
                      uint32_t *err_bits, void *stream) {
   g_err.clear();
   WorkNote work_note{c, (cudaStream_t)stream};
-  return transfer_states(c, ids, n, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
+  const int rc = transfer_states(c, ids, n, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream);
+  work_note.quiet = rc == PBDR_OK;   // the read synchronised its stream
+  return rc;
+}
+
+int pbdr_read_states_async(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *pos, float *vel,
+                           uint32_t *err_bits, void *stream) {
+  g_err.clear();
+  WorkNote work_note{c, (cudaStream_t)stream};
+  const int rc = transfer_states(c, ids, n, pos, vel, nullptr, nullptr, err_bits, 0, (cudaStream_t)stream,
+                                 nullptr, nullptr, false);
+  if (rc == PBDR_OK) {   // the scenes are in use until the stream reaches this point
+    stamp_use(c, ids, n, (cudaStream_t)stream);
+    work_note.quiet = true;
+  }
+  return rc;
 }
 
 int pbdr_write_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, const float *pos, const float *vel,

@@ -85,9 +85,10 @@ class Server:
                  clock: Callable[[], float] = time.perf_counter, stream=None,
                  bytes_per_particle: int = BYTES_PER_PARTICLE,
                  event_factory: Optional[Callable[[], object]] = None):
-        if event_factory is None and ctx_factory is None:
+        own_ctx = ctx_factory is None   # the library's own context (a GPU)
+        if event_factory is None and own_ctx:
             event_factory = CudaTimingEvent
-        if ctx_factory is None:
+        if own_ctx:
             from .binding import Context, OPT_AUTOTUNE, OPT_GRAPHS
 
             def ctx_factory():
@@ -107,9 +108,10 @@ class Server:
         self.results: Dict[int, tuple] = {}
         self.ledger = 0
         self.event_factory = event_factory
-        # finished states are read back into page-locked host buffers (grow-only)
-        self._pinned = ctx_factory is None
-        self._pin_pos = self._pin_vel = None
+        # finished states are read back into page-locked host buffers
+        # (grow-only), enqueued on the serving stream between two substeps
+        self._pinned = own_ctx
+        self._pin_pos = self._pin_vel = self._pin_err = None
         self._inflight: collections.deque = collections.deque()   # (start, end) events per tick
         self.tick_ms: List[float] = []
         self.host_ms = {"admit": 0.0, "step": 0.0, "retire": 0.0}
@@ -163,22 +165,49 @@ class Server:
             n += 1
         return n
 
-    def _retire(self):
+    def _take_done(self) -> List[Request]:
+        """Removes the requests that the last batched substep finished from
+        the resident set (they take no further substep)."""
         done = self._due.pop(self._stepped, [])   # in admission order
+        for req in done:
+            self._tick_work -= int(req.scene.num_particles) * int(req.scene.iterations)
+            del self.active[req.rid]
+            self._ids_dirty = True
+        return done
+
+    def _read_async(self, done: List[Request]):
+        """Enqueues the read of finished requests on the serving stream, after
+        the substep that finished them and before the next one (no kernel of
+        the next substep competes with it); returns (pos, vel, err, event) or
+        None where reads are synchronous (a context without asynchronous
+        reads, or no timing events)."""
+        if not (done and self._pinned and self.event_factory is not None):
+            return None
+        import torch
+        total = sum(int(r.scene.num_particles) for r in done)
+        if self._pin_pos is None or self._pin_pos.shape[0] < total:
+            cap = max(total, 2 * (0 if self._pin_pos is None else self._pin_pos.shape[0]))
+            self._pin_pos = torch.empty((cap, 3), dtype=torch.float32, pin_memory=True).numpy()
+            self._pin_vel = torch.empty((cap, 3), dtype=torch.float32, pin_memory=True).numpy()
+        if self._pin_err is None or self._pin_err.shape[0] < len(done):
+            cap = max(len(done), 2 * (0 if self._pin_err is None else self._pin_err.shape[0]))
+            self._pin_err = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        pos, vel, err = self._pin_pos[:total], self._pin_vel[:total], self._pin_err[:len(done)]
+        self.ctx.read_states_async([r.sid for r in done], pos, vel, err, stream=self.stream)
+        ev = self.event_factory()
+        ev.record(self.stream)
+        return pos, vel, err, ev
+
+    def _retire(self, done: List[Request], read=None):
+        """Delivers and frees finished requests: waits for their enqueued
+        read (`read` from _read_async), or reads them synchronously."""
         if not done:
             return
-        ids = [r.sid for r in done]
-        if self._pinned:
-            total = sum(int(r.scene.num_particles) for r in done)
-            if self._pin_pos is None or self._pin_pos.shape[0] < total:
-                import torch
-                cap = max(total, 2 * (0 if self._pin_pos is None else self._pin_pos.shape[0]))
-                self._pin_pos = torch.empty((cap, 3), dtype=torch.float32, pin_memory=True).numpy()
-                self._pin_vel = torch.empty((cap, 3), dtype=torch.float32, pin_memory=True).numpy()
-            pos, vel = self._pin_pos[:total], self._pin_vel[:total]
-            _, _, err = self.ctx.read_states(ids, pos, vel, stream=self.stream)
+        if read is not None:
+            pos, vel, err, ev = read
+            ev.synchronize()
         else:
-            pos, vel, err = self.ctx.read_states(ids, stream=self.stream)
+            pos, vel, err = self.ctx.read_states([r.sid for r in done], stream=self.stream)
         now = self.clock() - self.t0              # the results are on the host now
         at = 0
         for k, req in enumerate(done):
@@ -187,10 +216,7 @@ class Server:
             at += n
             self.ctx.destroy_scene(req.sid)
             self.ledger -= self._cost(req)
-            self._tick_work -= n * int(req.scene.iterations)
-            self._ids_dirty = True
             req.done = now
-            del self.active[req.rid]
             self.finished.append(req)
 
     # ---- main loop -----------------------------------------------------------
@@ -203,8 +229,16 @@ class Server:
             self.tick_ms.append(float(ev0.elapsed_time(ev1)))
 
     def tick(self) -> bool:
-        """One batched substep + admission + retirement round; False when idle."""
+        """One batched substep + retirement + admission round; False when idle.
+
+        The requests the previous substep finished leave the resident set
+        first and their read is enqueued, then the next substep (both
+        asynchronous, on the serving stream); only then does the host wait
+        for the read, deliver and free them and admit new requests, so that
+        host work overlaps the substep on the device."""
         t_0 = self.clock()
+        done = self._take_done()
+        read = self._read_async(done)
         stepped = bool(self.active)
         if stepped:
             if self._ids_dirty:
@@ -221,16 +255,16 @@ class Server:
             self._stepped += 1
             self.work_done += self._tick_work
         t_a = self.clock()
-        self._admit(t_a - self.t0)                 # host work overlaps the substep
+        self._retire(done, read)                   # waits for the read only
         t_b = self.clock()
-        self._retire()                             # reads back finished ones (synchronises)
+        self._admit(t_b - self.t0)                 # host work overlaps the substep
         self._drain(keep=1)                        # at most one substep ahead of the device
         t_c = self.clock()
         if not stepped:
             return bool(self.pending or self.active)
         self.host_ms["step"] += (t_a - t_0) * 1e3
-        self.host_ms["admit"] += (t_b - t_a) * 1e3
-        self.host_ms["retire"] += (t_c - t_b) * 1e3
+        self.host_ms["retire"] += (t_b - t_a) * 1e3
+        self.host_ms["admit"] += (t_c - t_b) * 1e3
         if self.event_factory is None:
             self.tick_ms.append((t_c - t_0) * 1e3)
         self.ticks += 1

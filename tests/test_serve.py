@@ -133,6 +133,7 @@ def test_results_identical_alone_and_in_the_mix(pbdr_lib):
     ids = [srv.submit(sc, steps, arrival=t) for sc, steps, t in reqs]
     st = srv.run(realtime=True)
     assert st["requests"] == len(reqs)
+    assert srv._pin_err is not None   # results came through the asynchronous page-locked read
     for rid, (sc, steps, _) in zip(ids, reqs):
         with pbdr_lib.Context(0) as c:
             sid = c.create_scene(sc)
@@ -167,3 +168,41 @@ def test_served_results_match_oracle(pbdr_lib, orc):
         o.substep(steps)
         dx = np.abs(gpos - o.x).max()
         assert dx <= 1e-5, f"request {rid} ({sc.num_particles} particles, {steps} substeps): |dx| {dx:.2e}"
+
+
+@pytest.mark.gpu
+def test_async_read_equals_sync_read(pbdr_lib):
+    """pbdr_read_states_async into page-locked buffers, completed by an event
+    on the same stream, gives the same bytes and error bits as the
+    synchronous batched read; scenes read this way and destroyed after the
+    event free ranges that a new scene can take."""
+    import torch
+    c = pbdr_lib.Context(0)
+    scs = [scenes.random_bodies_scene(seed=300 + k, num_bodies=6 + k) for k in range(5)]
+    ids = [c.create_scene(sc) for sc in scs]
+    st = torch.cuda.Stream()
+    c.step(ids, 4, st.cuda_stream)
+    pick = [ids[3], ids[0], ids[4]]
+    total = sum(scs[ids.index(i)].num_particles for i in pick)
+    pos = torch.empty((total, 3), dtype=torch.float32, pin_memory=True).numpy()
+    vel = torch.empty((total, 3), dtype=torch.float32, pin_memory=True).numpy()
+    err = torch.zeros(len(pick), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    c.read_states_async(pick, pos, vel, err, stream=st.cuda_stream)
+    ev = torch.cuda.Event()
+    ev.record(st)
+    c.step([ids[1], ids[2]], 2, st.cuda_stream)      # other scenes keep stepping
+    ev.synchronize()
+    spos, svel, serr = c.read_states(pick, stream=st.cuda_stream)
+    assert np.array_equal(pos, spos) and np.array_equal(vel, svel)
+    assert np.array_equal(err, serr) and not err.any()
+    for i in pick:
+        c.destroy_scene(i)
+    sid = c.create_scene(scs[0])                    # takes freed ranges
+    c.step([sid], 3, st.cuda_stream)
+    p2, v2, e2 = c.read_state(sid, stream=st.cuda_stream)
+    with pbdr_lib.Context(0) as a:
+        s0 = a.create_scene(scs[0])
+        a.step(s0, 3)
+        p0, v0, e0 = a.read_state(s0)
+    assert e2 == e0 == 0 and np.array_equal(p2, p0) and np.array_equal(v2, v0)
+    c.close()
