@@ -11,6 +11,9 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -65,6 +68,76 @@ struct PinnedBuf {
 // memory may make the driver synchronise with the stream it is issued on,
 // which would hold the host until earlier work there (a substep) finishes.
 // A slot is reused once the copy that last read it has completed.
+// A few host threads kept for the lifetime of a context, so that scene
+// set-up can split its per-particle pass without starting threads per call.
+// run(n, f) calls f(0) .. f(n-1) on the workers and the calling thread and
+// returns when all have finished.
+class HostPool {
+ public:
+  explicit HostPool(int workers) {
+    for (int i = 0; i < workers; ++i) th_.emplace_back([this] { loop(); });
+  }
+  HostPool(const HostPool &) = delete;
+  HostPool &operator=(const HostPool &) = delete;
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto &t : th_) t.join();
+  }
+  int size() const { return (int)th_.size() + 1; }
+  void run(int n, const std::function<void(int)> &f) {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      job_ = &f;
+      n_ = n;
+      next_ = 0;
+      left_ = n;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(m_);
+    done_.wait(g, [this] { return left_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  // takes and runs tasks of the current job until none is left
+  void work() {
+    for (;;) {
+      const std::function<void(int)> *f;
+      int t;
+      {
+        std::lock_guard<std::mutex> g(m_);
+        if (!job_ || next_ >= n_) return;
+        f = job_;
+        t = next_++;
+      }
+      (*f)(t);
+      std::lock_guard<std::mutex> g(m_);
+      if (--left_ == 0) done_.notify_all();
+    }
+  }
+  void loop() {
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(m_);
+        cv_.wait(g, [this] { return stop_ || (job_ && next_ < n_); });
+        if (stop_) return;
+      }
+      work();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex m_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)> *job_ = nullptr;
+  int n_ = 0, next_ = 0, left_ = 0;
+  bool stop_ = false;
+};
+
 struct StageRing {
   static constexpr int kSlots = 8;
   PinnedBuf buf[kSlots];
@@ -250,6 +323,8 @@ struct pbdr_ctx {
   int32_t ccap = 0, nc_used = 0;   // chunk (and partial-slot) capacity / use
   cudaStream_t cls_stream[kNumClasses] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kNumClasses] = {};
+  cudaStream_t rest_stream = nullptr;   // the streaming form of a mixed plan, beside the classes
+  cudaEvent_t ev_rest_join = nullptr;
   int path = 0;                    // 0: scene-resident where a scene fits, 1: streaming only
   bool use_graphs = true;          // replay a captured CUDA graph per substep
   bool autotune = true;            // time launch shapes on the first step of a plan
@@ -275,6 +350,7 @@ struct pbdr_ctx {
   // scene uploads: pinned staging
   PinnedBuf up_stage;
   StageRing h2d_ring;              // small tables of other calls
+  std::unique_ptr<HostPool> pool;  // host threads of scene set-up (started on first use)
   // stage profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -305,6 +381,16 @@ int dev_alloc(pbdr_ctx *c, DevBuf &b, size_t bytes) {
   b.bytes = bytes;
   c->used += bytes;
   return PBDR_OK;
+}
+
+// grow-only scratch with 50 % headroom (within the budget), so that a
+// working set that grows a little at a time (a server's resident requests)
+// reallocates rarely: freeing the old buffer waits for the device
+int dev_reserve(pbdr_ctx *c, DevBuf &b, size_t bytes) {
+  if (b.bytes >= bytes) return PBDR_OK;
+  const size_t want = bytes + bytes / 2;
+  if (!c->budget || c->used - b.bytes + want <= c->budget) return dev_alloc(c, b, want);
+  return dev_alloc(c, b, bytes);
 }
 
 void dev_free(pbdr_ctx *c, DevBuf &b) {
@@ -726,21 +812,21 @@ int activate(pbdr_ctx *c, Plan *P, cudaStream_t s) {
   int rc;
   if (S && S->np > 0) {
     const size_t npb = (size_t)S->np;
-    if ((rc = dev_alloc(c, c->s_keys_a, npb * 4)) || (rc = dev_alloc(c, c->s_keys_b, npb * 4)) ||
-        (rc = dev_alloc(c, c->s_vals_a, npb * 4)) || (rc = dev_alloc(c, c->s_vals_b, npb * 4)) ||
-        (rc = dev_alloc(c, c->s_spos, npb * sizeof(float4))) ||
-        (rc = dev_alloc(c, c->s_hist, radix_hist_words(S->np) * 4)) ||
-        (rc = dev_alloc(c, c->s_cells, (size_t)std::max<uint32_t>(S->T_total, 1) * sizeof(uint4))))
+    if ((rc = dev_reserve(c, c->s_keys_a, npb * 4)) || (rc = dev_reserve(c, c->s_keys_b, npb * 4)) ||
+        (rc = dev_reserve(c, c->s_vals_a, npb * 4)) || (rc = dev_reserve(c, c->s_vals_b, npb * 4)) ||
+        (rc = dev_reserve(c, c->s_spos, npb * sizeof(float4))) ||
+        (rc = dev_reserve(c, c->s_hist, radix_hist_words(S->np) * 4)) ||
+        (rc = dev_reserve(c, c->s_cells, (size_t)std::max<uint32_t>(S->T_total, 1) * sizeof(uint4))))
       return rc;
-    if (!S->pcontig && (rc = dev_alloc(c, c->s_pmap, npb * 4))) return rc;
-    if (!S->bcontig && (rc = dev_alloc(c, c->s_bmap, (size_t)std::max(S->nb, 1) * 4))) return rc;
+    if (!S->pcontig && (rc = dev_reserve(c, c->s_pmap, npb * 4))) return rc;
+    if (!S->bcontig && (rc = dev_reserve(c, c->s_bmap, (size_t)std::max(S->nb, 1) * 4))) return rc;
     const size_t nbod = (size_t)std::max(c->bcap, 1);
-    if ((rc = dev_alloc(c, c->s_bounds, nbod * 2 * sizeof(float4))) ||
-        (rc = dev_alloc(c, c->s_near, nbod * kNearMax * sizeof(int32_t))))
+    if ((rc = dev_reserve(c, c->s_bounds, nbod * 2 * sizeof(float4))) ||
+        (rc = dev_reserve(c, c->s_near, nbod * kNearMax * sizeof(int32_t))))
       return rc;
   }
   if (!P->tab.empty()) {
-    if ((rc = dev_alloc(c, c->tab, P->tab.size() * 4))) return rc;
+    if ((rc = dev_reserve(c, c->tab, P->tab.size() * 4))) return rc;
     if ((rc = staged_h2d(c, c->tab.p, P->tab.data(), P->tab.size() * 4, s))) return rc;
   }
   if (S && S->np > 0) {
@@ -920,6 +1006,8 @@ int ensure_class_streams(pbdr_ctx *c) {
     CUDA_TRY(cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming));
   }
+  CUDA_TRY(cudaStreamCreateWithFlags(&c->rest_stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&c->ev_rest_join, cudaEventDisableTiming));
   return PBDR_OK;
 }
 
@@ -1127,6 +1215,12 @@ int adjoint_substep(pbdr_ctx *c, Plan &P, const StateSlots &S, int it0, cudaStre
 int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
   int rc = ensure_class_streams(c);
   if (rc) return rc;
+  // the scenes above the largest class (the streaming form, P.rest) touch
+  // no scene, body or particle range of the classes: they run on a stream
+  // of their own beside the classes and fill the SMs the classes' last
+  // persistent CTAs leave idle.  With stage profiling on they run after the
+  // classes instead, so that the stages' times stay apart.
+  const bool rest_beside = P.rest && !c->profiling;
   {
     StageTimer tm(c, s, 5, launches);
     CUDA_TRY(cudaMemsetAsync(c->tickets.p, 0, 64, s));
@@ -1138,12 +1232,18 @@ int fused_substep(pbdr_ctx *c, Plan &P, cudaStream_t s, int64_t &launches) {
       launches += launch_class(c, P, k, c->cls_stream[k]);
       CUDA_TRY(cudaEventRecord(c->ev_join[k], c->cls_stream[k]));
     }
+    if (rest_beside) {
+      CUDA_TRY(cudaStreamWaitEvent(c->rest_stream, c->ev_fork, 0));
+      if ((rc = substep(c, *P.rest, c->rest_stream, launches))) return rc;
+      CUDA_TRY(cudaEventRecord(c->ev_rest_join, c->rest_stream));
+      CUDA_TRY(cudaStreamWaitEvent(s, c->ev_rest_join, 0));
+    }
     for (int k = 0; k < (int)P.classes.size(); ++k)
       if (P.classes[k].n) CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[k], 0));
     CUDA_TRY(cudaGetLastError());
   }
   c->last_fused_plan = &P;
-  if (P.rest) return substep(c, *P.rest, s, launches);
+  if (P.rest && !rest_beside) return substep(c, *P.rest, s, launches);
   return PBDR_OK;
 }
 
@@ -1435,10 +1535,10 @@ int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, 
   int rc;
   const bool want_pos = unpack ? cpos != nullptr : hpos != nullptr;
   const bool want_vel = unpack ? cvel != nullptr : hvel != nullptr;
-  if ((rc = dev_alloc(c, c->seg_p0, (size_t)n * 4))) return rc;
-  if ((rc = dev_alloc(c, c->seg_off, (size_t)(n + 1) * 8))) return rc;
-  if (want_pos && (rc = dev_alloc(c, c->stage_pos, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
-  if (want_vel && (rc = dev_alloc(c, c->stage_vel, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
+  if ((rc = dev_reserve(c, c->seg_p0, (size_t)n * 4))) return rc;
+  if ((rc = dev_reserve(c, c->seg_off, (size_t)(n + 1) * 8))) return rc;
+  if (want_pos && (rc = dev_reserve(c, c->stage_pos, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
+  if (want_vel && (rc = dev_reserve(c, c->stage_vel, (size_t)std::max<int64_t>(total, 1) * 12))) return rc;
   if ((rc = staged_h2d(c, c->seg_p0.p, p0.data(), (size_t)n * 4, s))) return rc;
   if ((rc = staged_h2d(c, c->seg_off.p, off.data(), (size_t)(n + 1) * 8, s))) return rc;
   PackArgs pa{};
@@ -1461,8 +1561,8 @@ int transfer_states(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, float *hpos, 
   if (want_pos) CUDA_TRY(cudaMemcpyAsync(hpos, pa.hpos, (size_t)total * 12, cudaMemcpyDeviceToHost, s));
   if (want_vel) CUDA_TRY(cudaMemcpyAsync(hvel, pa.hvel, (size_t)total * 12, cudaMemcpyDeviceToHost, s));
   if (err_bits) {
-    if ((rc = dev_alloc(c, c->err_ids, (size_t)n * 4))) return rc;
-    if ((rc = dev_alloc(c, c->err_out, (size_t)n * 4))) return rc;
+    if ((rc = dev_reserve(c, c->err_ids, (size_t)n * 4))) return rc;
+    if ((rc = dev_reserve(c, c->err_out, (size_t)n * 4))) return rc;
     if ((rc = staged_h2d(c, c->err_ids.p, ids, (size_t)n * 4, s))) return rc;
     k_errs<<<(n + 255) / 256, 256, 0, s>>>(c->scene_err.as<uint32_t>(), c->err_ids.as<int32_t>(), n,
                                             c->err_out.as<uint32_t>());
@@ -1506,6 +1606,8 @@ int pbdr_ctx_destroy(pbdr_ctx *c) {
     if (e) cudaEventDestroy(e);
   for (auto &w : c->work_ev) cudaEventDestroy(w.second);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->rest_stream) cudaStreamDestroy(c->rest_stream);
+  if (c->ev_rest_join) cudaEventDestroy(c->ev_rest_join);
   for (int k = 0; k < kNumClasses; ++k) {
     if (c->cls_stream[k]) cudaStreamDestroy(c->cls_stream[k]);
     if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
@@ -1666,24 +1768,31 @@ int pbdr_create_scene(pbdr_ctx *c, const pbdr_scene_desc *d, pbdr_scene *out) {
     }
   };
   {
-    const int hw = std::max(1, (int)std::thread::hardware_concurrency());
-    // host threads only for large scenes (starting them costs more than the
-    // pass saves below ~64k particles)
-    const int nthr = N >= 65536 ? std::max(1, std::min({8, hw, N / 16384})) : 1;
+    // scenes of 16k particles and more split their bodies over the
+    // context's host threads (started once, kept with the context)
+    int nthr = 1;
+    if (N >= 16384 && B > 1) {
+      if (!c->pool) {
+        const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+        c->pool.reset(new HostPool(std::max(0, std::min(7, hw - 1))));
+      }
+      nthr = std::max(1, std::min({c->pool->size(), N / 8192, (int)B}));
+    }
     std::vector<std::array<int, 2>> bad(nthr, std::array<int, 2>{0, 0});
     if (nthr == 1) {
       rest_pass(0, B, bad[0].data());
     } else {   // contiguous body ranges of about N / nthr particles each
-      std::vector<std::thread> pool;
-      int32_t b_begin = 0;
-      for (int t = 0; t < nthr && b_begin < B; ++t) {
+      std::vector<int32_t> cut(nthr + 1, B);
+      cut[0] = 0;
+      for (int t = 0; t + 1 < nthr; ++t) {
         const int64_t target = (int64_t)N * (t + 1) / nthr;
-        int32_t b_end = b_begin + 1;
-        while (b_end < B && (t == nthr - 1 || d->body_off[b_end] < target)) ++b_end;
-        pool.emplace_back(rest_pass, b_begin, b_end, bad[t].data());
-        b_begin = b_end;
+        int32_t b = std::max(cut[t], (int32_t)0);
+        while (b < B && d->body_off[b] < target) ++b;
+        cut[t + 1] = b;
       }
-      for (auto &th : pool) th.join();
+      c->pool->run(nthr, [&](int t) {
+        if (cut[t] < cut[t + 1]) rest_pass(cut[t], cut[t + 1], bad[t].data());
+      });
     }
     int bad_mass = 0, bad_finite = 0;
     for (const auto &f : bad) {
