@@ -56,11 +56,12 @@ def parse_args():
     ap.add_argument("--cpu-substeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample-scenes", type=int, default=256)
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival trace of the serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0,
                     help="Poisson arrival rate of the serving run (the serving workload's 2000/s)")
-    ap.add_argument("--serve-pool", type=int, default=32)
+    ap.add_argument("--serve-pool", type=int, default=256,
+                    help="distinct seeded requests the trace draws from")
     ap.add_argument("--serve-budget-gb", type=int, default=120)
     ap.add_argument("--path", choices=["resident", "streaming"], default="resident",
                     help="timed path: scene-resident kernel where scenes fit (default) or the "
@@ -653,15 +654,19 @@ def run_serving(args, local_rank):
     pick = rng.integers(0, len(pool), size=len(arrivals))
     steps = rng.integers(1, 101, size=len(arrivals))
     stream = torch.cuda.Stream()
+    errs = [0]
+
+    def delivered(rid, pos, vel, err):   # results are delivered, not kept (20k requests)
+        errs[0] += 1 if err else 0
     srv = Server(hbm_budget_bytes=args.serve_budget_gb << 30, device=local_rank,
-                 stream=stream.cuda_stream)
+                 stream=stream.cuda_stream, on_result=delivered)
     offered = 0
     for t, k, st in zip(arrivals, pick, steps):
         srv.submit(pool[k], int(st), arrival=float(t))
         offered += pool[k].num_particles * pool[k].iterations * int(st)
     with torch.cuda.stream(stream):
         stats = srv.run(realtime=True)
-    errs = sum(1 for r in srv.results.values() if r[2])
+    errs = errs[0]
     return {
         "requests": stats["requests"], "arrival_rate_hz": args.serve_rate,
         "trace_s": args.serve_seconds, "budget_gb": args.serve_budget_gb,

@@ -77,14 +77,17 @@ class Server:
     ``event_factory`` returns a timing event with ``record(stream)``,
     ``synchronize()`` and ``elapsed_time(end)`` in ms (CUDA events of the
     serving stream by default; with a fake context and no factory, ticks are
-    timed on the host clock).
+    timed on the host clock).  ``on_result(rid, pos, vel, err_bits)``, if
+    given, receives every finished request instead of ``results``: pos and
+    vel are views that stay valid only during the call (copy what is kept).
     """
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, device: int = 0,
                  ctx_factory: Optional[Callable[[], object]] = None,
                  clock: Callable[[], float] = time.perf_counter, stream=None,
                  bytes_per_particle: int = BYTES_PER_PARTICLE,
-                 event_factory: Optional[Callable[[], object]] = None):
+                 event_factory: Optional[Callable[[], object]] = None,
+                 on_result: Optional[Callable[[int, np.ndarray, np.ndarray, int], None]] = None):
         own_ctx = ctx_factory is None   # the library's own context (a GPU)
         if event_factory is None and own_ctx:
             event_factory = CudaTimingEvent
@@ -108,6 +111,7 @@ class Server:
         self.results: Dict[int, tuple] = {}
         self.ledger = 0
         self.event_factory = event_factory
+        self.on_result = on_result
         # finished states are read back into page-locked host buffers
         # (grow-only), enqueued on the serving stream between two substeps
         self._pinned = own_ctx
@@ -212,7 +216,10 @@ class Server:
         at = 0
         for k, req in enumerate(done):
             n = int(req.scene.num_particles)
-            self.results[req.rid] = (pos[at:at + n].copy(), vel[at:at + n].copy(), int(err[k]))
+            if self.on_result is not None:
+                self.on_result(req.rid, pos[at:at + n], vel[at:at + n], int(err[k]))
+            else:
+                self.results[req.rid] = (pos[at:at + n].copy(), vel[at:at + n].copy(), int(err[k]))
             at += n
             self.ctx.destroy_scene(req.sid)
             self.ledger -= self._cost(req)
