@@ -205,8 +205,9 @@ int pbdr_read_neighbors(pbdr_ctx *ctx, pbdr_scene scene, uint32_t *sorted_key,
 /* PBDR_OPT_GRAPHS: 1 (default) = the first pbdr_step of a scene set captures
  *   one substep into a CUDA graph and every substep replays it (not on the
  *   legacy NULL stream, and not while stage timing is on); 0 = plain launches.
- * PBDR_OPT_AUTOTUNE: 1 (default) = once a scene set has run 128 substeps
- *   (contacts have formed), the scene-resident kernel's launch shapes are
+ * PBDR_OPT_AUTOTUNE: 1 (default) = once a scene set has run
+ *   PBDR_OPT_TUNE_AFTER substeps (contacts have formed), the scene-resident
+ *   kernel's launch shapes are
  *   timed per size class with at least as many scenes as SMs (threads per
  *   CTA, scratch and velocities in shared or global memory, CTAs per SM), on
  *   whole substeps from the same saved state whose effects are undone, and
@@ -214,6 +215,10 @@ int pbdr_read_neighbors(pbdr_ctx *ctx, pbdr_scene scene, uint32_t *sorted_key,
  *   sizes); results do not depend on the shape. */
 #define PBDR_OPT_GRAPHS 3
 #define PBDR_OPT_AUTOTUNE 4
+/* PBDR_OPT_TUNE_AFTER: substeps a scene set runs before its launch shapes are
+ *   tuned, >= 1 (default 128): a state close to the one that will be stepped
+ *   most (bodies at rest after a drop, say) gives the most useful timings. */
+#define PBDR_OPT_TUNE_AFTER 5
 int pbdr_set_option(pbdr_ctx *ctx, int32_t option, int64_t value);
 
 /* Tangent-linear (forward-mode) substeps: the derivative of Algorithm 1's

@@ -41,6 +41,7 @@ OPT_PATH = 1
 OPT_FUSED_THREADS = 2
 OPT_GRAPHS = 3
 OPT_AUTOTUNE = 4
+OPT_TUNE_AFTER = 5
 
 
 class PbdrError(RuntimeError):

@@ -276,7 +276,7 @@ struct Plan {
 };
 
 constexpr size_t kMaxCachedPlans = 1024;
-constexpr int64_t kTuneAfter = 128;   // substeps of a plan before its launch shapes are tuned
+constexpr int64_t kTuneAfter = 128;   // default substeps of a plan before its launch shapes are tuned
 
 constexpr int kClassCaps[kNumClasses] = {1024, 2048, 4096, 8192};
 constexpr int kClassThreads[kNumClasses] = {256, 256, 512, 512};
@@ -328,6 +328,7 @@ struct pbdr_ctx {
   int path = 0;                    // 0: scene-resident where a scene fits, 1: streaming only
   bool use_graphs = true;          // replay a captured CUDA graph per substep
   bool autotune = true;            // time launch shapes on the first step of a plan
+  int64_t tune_after = kTuneAfter; // substeps of a plan before it is tuned
   int fused_threads = 0;           // 0: per-class default
   int num_sms = 0;
   Plan *last_fused_plan = nullptr;
@@ -1992,9 +1993,9 @@ int pbdr_step(pbdr_ctx *c, const pbdr_scene *ids, int32_t n, int32_t substeps, v
     P->graph = nullptr;
   }
   for (int32_t k = 0; k < substeps; ++k) {
-    // launch shapes are tuned once the plan has run kTuneAfter substeps,
+    // launch shapes are tuned once the plan has run tune_after substeps,
     // on a state where contacts have formed
-    if (P->fused && c->autotune && !P->tuned && P->substeps_run >= kTuneAfter) {
+    if (P->fused && c->autotune && !P->tuned && P->substeps_run >= c->tune_after) {
       if ((rc = autotune_fused(c, *P, s))) return rc;
       if (P->graph) cudaGraphExecDestroy(P->graph);
       P->graph = nullptr;
@@ -2411,6 +2412,10 @@ int pbdr_set_option(pbdr_ctx *c, int32_t option, int64_t value) {
       break;
     case PBDR_OPT_AUTOTUNE:
       c->autotune = value != 0;
+      break;
+    case PBDR_OPT_TUNE_AFTER:
+      if (value < 1) return fail(PBDR_ERR_INVALID, "PBDR_OPT_TUNE_AFTER takes a substep count >= 1");
+      c->tune_after = value;
       break;
     case PBDR_OPT_FUSED_THREADS:
       if (value != 0 && (value < 32 || value > 512 || value % 32))

@@ -373,6 +373,31 @@ def test_graph_replay_and_autotune_are_bit_identical(pbdr_lib, streaming):
             assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
 
 
+@pytest.mark.gpu
+def test_tune_after_option(pbdr_lib):
+    """PBDR_OPT_TUNE_AFTER takes a substep count >= 1; a scene set tuned
+    after 5 substeps ends bit-identical to the same set never tuned."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    scs = [scenes.batch_scene(rng) for _ in range(400)]
+    outs, cfgs = [], []
+    for tune in (0, 1):
+        with pbdr_lib.Context(0) as c:
+            with pytest.raises(RuntimeError):
+                c.set_option(pbdr_lib.OPT_TUNE_AFTER, 0)
+            c.set_option(pbdr_lib.OPT_AUTOTUNE, tune)
+            c.set_option(pbdr_lib.OPT_TUNE_AFTER, 5)
+            ids = [c.create_scene(s) for s in scs]
+            st = torch.cuda.Stream()
+            c.step(ids, 4, st.cuda_stream)
+            c.step(ids, 6, st.cuda_stream)   # tuned at its second substep when tune == 1
+            outs.append([c.read_state(i, st.cuda_stream)[:2] for i in ids])
+            cfgs.append(c.plan_config(ids))
+    assert any(k["scenes"] >= 152 for k in cfgs[1])   # a class was large enough to tune
+    for (p0, v0), (p1, v1) in zip(outs[0], outs[1]):
+        assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
+
+
 def _two_particle_scene(pos, vel, inv_mass, plane, dt):
     pos = np.asarray(pos, np.float32)
     return scenes.Scene(pos=pos, vel=np.asarray(vel, np.float32), inv_mass=np.asarray(inv_mass, np.float32),
