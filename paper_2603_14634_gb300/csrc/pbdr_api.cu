@@ -343,6 +343,7 @@ struct pbdr_ctx {
   // tables of the active plan and the streaming form's scratch (grow-only)
   DevBuf tab, s_keys_a, s_keys_b, s_vals_a, s_vals_b, s_hist, s_cells, s_spos, s_pmap, s_bmap;
   DevBuf s_bounds, s_near;         // streaming neighbour culling: body boxes, near bodies
+  DevBuf s_ilist, s_icount;        // ... and the particles it leaves to search, their number
   const Plan *active = nullptr;
   uint64_t gen = 1;                // bumped whenever a device buffer moves (graphs recapture)
   Plan *last_nbr_plan = nullptr;
@@ -823,7 +824,8 @@ int activate(pbdr_ctx *c, Plan *P, cudaStream_t s) {
     if (!S->bcontig && (rc = dev_reserve(c, c->s_bmap, (size_t)std::max(S->nb, 1) * 4))) return rc;
     const size_t nbod = (size_t)std::max(c->bcap, 1);
     if ((rc = dev_reserve(c, c->s_bounds, nbod * 2 * sizeof(float4))) ||
-        (rc = dev_reserve(c, c->s_near, nbod * kNearMax * sizeof(int32_t))))
+        (rc = dev_reserve(c, c->s_near, nbod * kNearMax * sizeof(int32_t))) ||
+        (rc = dev_reserve(c, c->s_ilist, npb * sizeof(int32_t))) || (rc = dev_reserve(c, c->s_icount, 16)))
       return rc;
   }
   if (!P->tab.empty()) {
@@ -881,7 +883,8 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
   StageTimer tm(c, s, 3, launches);
   // body boxes and near bodies: particles far from every other body skip the search
   const bool cull = c->s_bounds.bytes >= (size_t)c->bcap * 2 * sizeof(float4) &&
-                    c->s_near.bytes >= (size_t)c->bcap * kNearMax * sizeof(int32_t);
+                    c->s_near.bytes >= (size_t)c->bcap * kNearMax * sizeof(int32_t) &&
+                    c->s_ilist.bytes >= (size_t)P.np * sizeof(int32_t) && c->s_icount.p;
   if (cull) {
     BoundArgs ba{};
     ba.Xp = Xp;
@@ -930,8 +933,12 @@ int neighbor_stage(pbdr_ctx *c, Plan &P, const float4 *Xp, cudaStream_t s, int64
     na.bounds = c->s_bounds.as<float4>();
     na.near = c->s_near.as<int32_t>();
     na.quat = c->quat.as<float4>();
+    na.ilist = c->s_ilist.as<int32_t>();
+    na.icount = c->s_icount.as<uint32_t>();
+    CUDA_TRY(cudaMemsetAsync(c->s_icount.p, 0, 4, s));
   }
-  launches += launch_neighbors(na, s);
+  if (!c->num_sms) CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  launches += launch_neighbors(na, c->num_sms, s);
   c->last_nbr_plan = &P;
   return PBDR_OK;
 }

@@ -121,6 +121,10 @@ struct NbrArgs {
   const float4 *bounds;
   const int32_t *near;
   const float4 *quat;
+  // with culling: the particles within reach of another body (the search
+  // list, global ids) and their number (zero before k_interface)
+  int32_t *ilist;
+  uint32_t *icount;
 };
 
 // per-body bounding boxes and near-body lists of the streaming neighbour stage
@@ -243,7 +247,7 @@ struct PackArgs {
 
 int launch_predict(const PredictArgs &a, cudaStream_t s);
 int launch_cells(const CellArgs &a, cudaStream_t s);
-int launch_neighbors(const NbrArgs &a, cudaStream_t s);
+int launch_neighbors(const NbrArgs &a, int num_sms, cudaStream_t s);
 int launch_body_bounds(const BoundArgs &a, cudaStream_t s);
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s);
 int launch_iterate_tangent(const IterArgs &a, const TangentArgs &t, cudaStream_t s);

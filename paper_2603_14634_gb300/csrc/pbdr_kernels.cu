@@ -204,36 +204,27 @@ __global__ void __launch_bounds__(128) k_near_bodies(BoundArgs a) {
   a.bounds[2 * (int64_t)b + 1] = e;
 }
 
-__global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
-  // threads walk the particles in caller order: the particles of a body are
-  // contiguous and close in space, so a warp's bucket lookups coincide
-  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.np) return;
-  const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
-  const float4 xp = a.Xp[p];
-  const int32_t bp = a.pbody[p];
-  const int32_t s = a.bodies[bp].scene;
-  const ScenePar sp = a.scenes[s];
-  if (a.bounds) {
-    // a particle farther than R_n from the box of every body near its own
-    // has no neighbour: skip the 27-cell search
-    const int nn = __float_as_int(a.bounds[2 * (int64_t)bp + 1].w);
-    if (nn <= kNearMax) {
-      const float reach = cull_reach(sp.Rn2);
-      bool iface = false;
-      for (int k = 0; k < nn && !iface; ++k) {
-        const int32_t bo = a.near[(int64_t)kNearMax * bp + k];
-        const float4 c4 = a.bounds[2 * (int64_t)bo], e4 = a.bounds[2 * (int64_t)bo + 1];
-        float R[9];
-        quat_to_mat(a.quat[bo], R);
-        iface = cull_near_box(f3(xp), f3(c4), f3(e4), R, reach);
-      }
-      if (!iface) {
-        a.nbr_cnt[p] = 0;
-        return;
-      }
-    }
+// true when particle p (predicted position xp, body bp) lies within R_n of
+// the box of a body near its own, or when its body has more near bodies
+// than are listed: only such a particle can have a neighbour
+__device__ __forceinline__ bool near_other_body(const NbrArgs &a, float4 xp, int32_t bp, const ScenePar &sp) {
+  const int nn = __float_as_int(a.bounds[2 * (int64_t)bp + 1].w);
+  if (nn > kNearMax) return true;
+  const float reach = cull_reach(sp.Rn2);
+  for (int k = 0; k < nn; ++k) {
+    const int32_t bo = a.near[(int64_t)kNearMax * bp + k];
+    const float4 c4 = a.bounds[2 * (int64_t)bo], e4 = a.bounds[2 * (int64_t)bo + 1];
+    float R[9];
+    quat_to_mat(a.quat[bo], R);
+    if (cull_near_box(f3(xp), f3(c4), f3(e4), R, reach)) return true;
   }
+  return false;
+}
+
+// the 27-cell search of particle p: its ascending list of particles of
+// other bodies within R_n, into nbr / nbr_cnt
+__device__ __forceinline__ void search_cells(const NbrArgs &a, int32_t p, float4 xp, int32_t bp, int32_t s,
+                                             const ScenePar &sp) {
   const uint32_t hb = a.hbase[s], mask = sp.T - 1u;
   const int32_t ix = cell_coord(xp.x, sp.inv_h), iy = cell_coord(xp.y, sp.inv_h),
                 iz = cell_coord(xp.z, sp.inv_h);
@@ -276,6 +267,52 @@ __global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
   for (int k = 0; k < nw; ++k) a.nbr[(int64_t)k * a.nbr_stride + p] = list[k];
   a.nbr_cnt[p] = nw;
   if (cnt > cap) atomicOr(&a.scene_err[s], (uint32_t)PBDR_EBIT_NBR_OVERFLOW);
+}
+
+// With culling: every particle near another body's box is appended to
+// ilist (one atomic per warp; lanes keep their order, so a warp's particles
+// stay together), every other one gets an empty list.
+__global__ void __launch_bounds__(128) k_interface(NbrArgs a) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  bool iface = false;
+  int32_t p = 0;
+  if (i < a.np) {
+    p = a.pmap ? a.pmap[i] : a.pbase + i;
+    const int32_t bp = a.pbody[p];
+    const ScenePar sp = a.scenes[a.bodies[bp].scene];
+    iface = near_other_body(a, a.Xp[p], bp, sp);
+    if (!iface) a.nbr_cnt[p] = 0;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, iface);
+  if (m == 0u) return;
+  uint32_t base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(a.icount, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+  if (iface) a.ilist[base + __popc(m & ((1u << lane) - 1u))] = p;
+}
+
+// The search: over the interface list (grid-stride, every lane busy) or,
+// without culling, one thread per particle.
+__global__ void __launch_bounds__(128) k_neighbors(NbrArgs a) {
+  if (a.ilist) {
+    const uint32_t n = *a.icount;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+      const int32_t p = a.ilist[k];
+      const int32_t bp = a.pbody[p];
+      const int32_t s = a.bodies[bp].scene;
+      search_cells(a, p, a.Xp[p], bp, s, a.scenes[s]);
+    }
+    return;
+  }
+  // threads walk the particles in caller order: the particles of a body are
+  // contiguous and close in space, so a warp's bucket lookups coincide
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  const int32_t p = a.pmap ? a.pmap[i] : a.pbase + i;
+  const int32_t bp = a.pbody[p];
+  const int32_t s = a.bodies[bp].scene;
+  search_cells(a, p, a.Xp[p], bp, s, a.scenes[s]);
 }
 
 
@@ -1225,10 +1262,18 @@ int launch_body_bounds(const BoundArgs &a, cudaStream_t s) {
   return 2;
 }
 
-int launch_neighbors(const NbrArgs &a, cudaStream_t s) {
+int launch_neighbors(const NbrArgs &a, int num_sms, cudaStream_t s) {
   if (a.np <= 0) return 0;
-  k_neighbors<<<blocks_for(a.np, 128), 128, 0, s>>>(a);
-  return 1;
+  if (!a.ilist) {
+    k_neighbors<<<blocks_for(a.np, 128), 128, 0, s>>>(a);
+    return 1;
+  }
+  k_interface<<<blocks_for(a.np, 128), 128, 0, s>>>(a);
+  // the list's length is known on the device only: a grid of 16 CTAs per SM
+  // walks it
+  const int grid = (int)std::min<int64_t>(blocks_for(a.np, 128), 16 * (int64_t)std::max(num_sms, 1));
+  k_neighbors<<<grid, 128, 0, s>>>(a);
+  return 2;
 }
 
 int launch_iterate(const IterArgs &a, int warps_per_block, cudaStream_t s) {
