@@ -1,7 +1,8 @@
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
 //
 // Per pass: (1) every 4096-key tile counts its digits in shared memory and
-// writes a digit-major histogram hist[digit][tile]; (2) an exclusive scan of
+// writes a digit-major histogram hist[digit][tile] (a thread loads its 16
+// keys of the tile at once, as the scatter below does); (2) an exclusive scan of
 // that histogram (reduce / top / down-sweep) gives each (digit, tile) its
 // first output slot; (3) every tile re-reads its keys in 16 rounds of 256 and
 // scatters them: within a round, lanes with equal digits are ranked with
@@ -25,13 +26,18 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint32_t *__restrict__ 
                                                    int ntiles) {
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
-  __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kTile;
-#pragma unroll 4
+  // the tile's keys are requested together: one memory round trip
+  uint32_t k[kItems];
+#pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    int64_t i = base + r * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+    const int64_t i = base + r * kThreads + threadIdx.x;
+    k[r] = i < n ? keys[i] : 0u;
   }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r)
+    if (base + r * kThreads + threadIdx.x < n) atomicAdd(&cnt[(k[r] >> shift) & 255u], 1u);
   __syncthreads();
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
@@ -125,6 +131,18 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *__restrict
   const uint32_t lt_mask = (1u << lane) - 1u;
   base[t] = offs[(int64_t)t * ntiles + blockIdx.x];
   const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  // the thread's keys and values of all rounds are requested together (one
+  // memory round trip per tile instead of one per round)
+  uint32_t kr[kItems], vr[kItems];
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t i = tile0 + r * kThreads + t;
+    if (i < n) {
+      kr[r] = kin[i];
+      vr[r] = vin[i];
+    }
+  }
+#pragma unroll
   for (int r = 0; r < kItems; ++r) {
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) wcnt[w][t] = 0u;
@@ -133,8 +151,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint32_t *__restrict
     const bool valid = i < n;
     uint32_t key = 0, val = 0, d = 256u;
     if (valid) {
-      key = kin[i];
-      val = vin[i];
+      key = kr[r];
+      val = vr[r];
       d = (key >> shift) & 255u;
     }
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
