@@ -55,8 +55,8 @@ def parse_args():
     ap.add_argument("--e2e-split", type=int, default=4,
                     help="contexts (each on its own stream) the end-to-end run splits the batch "
                          "over, so that one part's host copies overlap another part's substep")
-    ap.add_argument("--cpu-scenes", type=int, default=4096)
-    ap.add_argument("--cpu-substeps", type=int, default=4)
+    ap.add_argument("--cpu-scenes", type=int, default=256)
+    ap.add_argument("--cpu-substeps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample-scenes", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -118,21 +118,26 @@ def make_workload(args, seed):
 # CPU oracle timings (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_throughput(scs, substeps, threads):
-    """Times the FP64 oracle on the scenes (each advanced `substeps`),
-    spread over `threads` host threads (ctypes releases the GIL).
-    Returns (particle-iters/s, seconds, particle-iters)."""
+def oracle_scenes(scs, settle, threads):
+    """The FP64 oracle's copies of the scenes, advanced `settle` substeps
+    (untimed: the state the GPU arm times is the one after its settling)."""
     from oracle import oracle as O
     O.build()
     objs = [O.OracleScene(s) for s in scs]
+    if settle > 0:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda o: o.substep(settle), objs))
+    return objs
+
+
+def oracle_time(objs, scs, substeps, threads):
+    """Times the oracle advancing its scenes `substeps` further, spread over
+    `threads` host threads (ctypes releases the GIL).
+    Returns (particle-iters/s, seconds, particle-iters)."""
     work = sum(s.num_particles * s.iterations for s in scs) * substeps
-
-    def run(o):
-        o.substep(substeps)
-
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(run, objs))
+        list(ex.map(lambda o: o.substep(substeps), objs))
     dt = time.perf_counter() - t0
     return work / dt, dt, work
 
@@ -589,11 +594,13 @@ def run_pbdr(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         cpu_scs = scs[: args.cpu_scenes]
         thr = host_cores()
-        v, secs, work = oracle_throughput(cpu_scs, args.cpu_substeps, thr)
+        objs = oracle_scenes(cpu_scs, args.settle, thr)
+        v, secs, work = oracle_time(objs, cpu_scs, args.cpu_substeps, thr)
         line["cpu_baseline"] = {
             "value": round(v, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": (f"first {len(cpu_scs)} scenes of the workload x {args.cpu_substeps} "
-                       f"substeps from the seeded start, FP64 C oracle, one scene per host thread "
+            "sample": (f"first {len(cpu_scs)} scenes of the workload, settled {args.settle} substeps "
+                       f"by the oracle as the GPU arm's batch is, then {args.cpu_substeps} timed "
+                       f"substeps; FP64 C oracle, one scene per host thread "
                        f"({work} particle-iters in {secs:.1f} s)")}
     if dist is not None:
         dist.destroy_process_group()
@@ -730,18 +737,20 @@ def run_reference(args, rank):
     scs = make_workload(args, args.seed)
     sample = scs[: args.ref_sample_scenes]
     thr = host_cores()
+    objs = oracle_scenes(sample, args.settle, thr)   # the state the GPU arm times
     for _ in range(args.warmup):
-        oracle_throughput(sample, 1, thr)
+        oracle_time(objs, sample, 1, thr)
     times = []
     work = 0
     for _ in range(args.steps):
-        v, secs, w = oracle_throughput(sample, 1, thr)
+        v, secs, w = oracle_time(objs, sample, 1, thr)
         times.append(secs)
         work += w
     total = sum(times)
     value = work / total
     cpu = {"value": round(value, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
-           "sample": f"first {len(sample)} scenes of the workload, one substep per step, FP64 C oracle"}
+           "sample": (f"first {len(sample)} scenes of the workload, settled {args.settle} substeps by "
+                      f"the oracle as the GPU arm's batch is, then one substep per step, FP64 C oracle")}
     return {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
