@@ -83,6 +83,22 @@ def test_random_bodies_colliding(ctx, orc, seed):
     _compare_one_substep(ctx, orc, sc, (o.x, o.v), label=f"16 bodies colliding seed {seed}")
 
 
+def test_large_scene_set_up_on_host_threads(ctx, orc):
+    """A scene of 22 500 particles (above the size from which scene set-up
+    splits its rest-shape pass over the context's host threads) with uneven
+    particle masses: its state reads back exactly as given, and one substep
+    agrees with the oracle."""
+    sc = scenes.random_bodies_scene(seed=5, num_bodies=180)
+    rng = np.random.default_rng(5)
+    sc.inv_mass = rng.uniform(0.5, 2.0, sc.num_particles).astype(np.float32)
+    assert sc.num_particles >= 16384
+    sid = ctx.create_scene(sc)
+    pos, vel, err = ctx.read_state(sid)
+    assert err == 0 and np.array_equal(pos, sc.pos) and np.array_equal(vel, sc.vel)
+    ctx.destroy_scene(sid)
+    _compare_one_substep(ctx, orc, sc, label="22500 particles, uneven masses")
+
+
 def test_batched_scenes_one_substep(ctx, orc):
     rng = np.random.default_rng(11)
     scs = [scenes.batch_scene(rng) for _ in range(8)]

@@ -113,6 +113,26 @@ def test_late_arrivals_join_running_batches():
     assert st["latency_ms_p50"] is not None and st["tick_ms_p99"] >= st["tick_ms_p50"]
 
 
+def test_results_delivered_to_a_callback_are_not_kept():
+    """With on_result, every finished request is handed over once, with its
+    substep count in the fake's positions, and `results` stays empty."""
+    fake = FakeContext(capacity=50_000)
+    got = {}
+
+    def on_result(rid, pos, vel, err):
+        assert rid not in got
+        got[rid] = (int(pos[0, 0]), pos.shape[0], err)
+
+    srv = Server(hbm_budget_bytes=50_000, bytes_per_particle=1, ctx_factory=lambda: fake,
+                 clock=VirtualClock(), on_result=on_result)
+    want = {}
+    for k in range(12):
+        n, steps = 500 + 100 * k, 1 + k % 5
+        want[srv.submit(_S(n), steps, arrival=0.001 * k)] = (steps, n, 0)
+    srv.run(realtime=True)
+    assert got == want and not srv.results
+
+
 def test_poisson_trace_rate():
     t = poisson_trace(2000.0, 5.0, seed=0)
     assert abs(len(t) / 5.0 - 2000.0) < 100
